@@ -1,0 +1,171 @@
+"""CPU oracle for the zero-temperature checkerboard quench (arXiv:2305.12161).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this package.
+The product library (``paper_2305_12161_gb300``) never imports it and shares no code
+with it.
+
+The arithmetic lives in ``ising_oracle.c`` (one byte per spin, plain loops, every
+function citing the passage of the paper it follows); this module compiles it with the
+host C compiler and exposes it through ``ctypes``.
+
+Spin arrays are ``numpy.int8`` of shape ``(L, L, L)`` indexed ``[z, y, x]``, so that the
+flat C-order index is ``x + L*(y + L*z)``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ising_oracle.c")
+_LIB = os.path.join(_HERE, "libising_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+TIE_GLAUBER, TIE_ALWAYS, TIE_NEVER = 0, 1, 2
+
+
+def build(force: bool = False) -> str:
+    """Compile ``libising_oracle.so`` (with OpenMP when the compiler has it)."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    cc = os.environ.get("CC", "gcc")
+    base = [cc, "-O2", "-std=c11", "-fPIC", "-shared", _SRC, "-o", _LIB + ".tmp", "-lm"]
+    try:
+        subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True, capture_output=True)
+    os.replace(_LIB + ".tmp", _LIB)
+    return _LIB
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_LIB)
+            u32p = ctypes.POINTER(ctypes.c_uint32)
+            i64p = ctypes.POINTER(ctypes.c_int64)
+            i8p = ctypes.POINTER(ctypes.c_int8)
+            f64p = ctypes.POINTER(ctypes.c_double)
+            L.orc_set_threads.argtypes = [ctypes.c_int]
+            L.orc_set_threads.restype = ctypes.c_int
+            L.orc_philox4x32_10.argtypes = [u32p, u32p, u32p]
+            L.orc_philox4x32_10.restype = None
+            L.orc_rng_bit.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int64]
+            L.orc_rng_bit.restype = ctypes.c_int
+            L.orc_init.argtypes = [ctypes.c_int, ctypes.c_uint64, i8p]
+            L.orc_init.restype = None
+            L.orc_half_sweep.argtypes = [ctypes.c_int, i8p, ctypes.c_int, ctypes.c_uint32,
+                                         ctypes.c_uint64, ctypes.c_int, i64p, i64p]
+            L.orc_half_sweep.restype = ctypes.c_int64
+            L.orc_sweeps.argtypes = [ctypes.c_int, i8p, ctypes.c_uint32, ctypes.c_int64,
+                                     ctypes.c_uint64, ctypes.c_int]
+            L.orc_sweeps.restype = None
+            L.orc_record_len.argtypes = [ctypes.c_int]
+            L.orc_record_len.restype = ctypes.c_int64
+            L.orc_record.argtypes = [ctypes.c_int, i8p, ctypes.c_int64, i64p]
+            L.orc_record.restype = None
+            L.orc_derived.argtypes = [ctypes.c_int, i64p, ctypes.c_double, ctypes.c_int, f64p]
+            L.orc_derived.restype = None
+            _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray, ctype):
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def _check_lattice(s: np.ndarray) -> int:
+    if s.dtype != np.int8 or s.ndim != 3 or not (s.shape[0] == s.shape[1] == s.shape[2]):
+        raise ValueError("spins must be an int8 array of shape (L, L, L)")
+    if not s.flags.c_contiguous:
+        raise ValueError("spins must be C-contiguous")
+    return s.shape[0]
+
+
+def set_threads(n: int) -> int:
+    """Set the OpenMP thread count (<= 0 keeps the current); returns threads in use."""
+    return int(lib().orc_set_threads(int(n)))
+
+
+def philox4x32_10(ctr, key):
+    """Philox4x32-10 of a 4-word counter and a 2-word key; returns four uint32."""
+    c = np.asarray(ctr, dtype=np.uint32).copy()
+    k = np.asarray(key, dtype=np.uint32).copy()
+    o = np.zeros(4, dtype=np.uint32)
+    lib().orc_philox4x32_10(_p(c, ctypes.c_uint32), _p(k, ctypes.c_uint32), _p(o, ctypes.c_uint32))
+    return [int(v) for v in o]
+
+
+def rng_bit(S: int, t: int, phase: int, h: int) -> int:
+    return int(lib().orc_rng_bit(S % 2**64, t, phase, h))
+
+
+def init(L: int, seed: int, replica: int = 0) -> np.ndarray:
+    """T = infinity start of replica ``replica`` of a run seeded ``seed``."""
+    s = np.empty((L, L, L), dtype=np.int8)
+    lib().orc_init(L, (seed + replica) % 2**64, _p(s, ctypes.c_int8))
+    return s
+
+
+def half_sweep(s: np.ndarray, q: int, t: int, S: int, rule: int = TIE_GLAUBER):
+    """One half-sweep in place; returns (flips, incremental dB, incremental dM)."""
+    L = _check_lattice(s)
+    dB = ctypes.c_int64(0)
+    dM = ctypes.c_int64(0)
+    f = lib().orc_half_sweep(L, _p(s, ctypes.c_int8), q, t, S % 2**64, rule,
+                             ctypes.byref(dB), ctypes.byref(dM))
+    return int(f), int(dB.value), int(dM.value)
+
+
+def sweeps(s: np.ndarray, t0: int, n: int, S: int, rule: int = TIE_GLAUBER) -> None:
+    """``n`` MCS in place, starting at completed-sweep count ``t0``."""
+    L = _check_lattice(s)
+    lib().orc_sweeps(L, _p(s, ctypes.c_int8), t0, n, S % 2**64, rule)
+
+
+def record_len(L: int) -> int:
+    return int(lib().orc_record_len(L))
+
+
+def record(s: np.ndarray, t: int = 0) -> np.ndarray:
+    """Integer record [t, M, B, D_x(0..L/2), D_y(0..L/2), D_z(0..L/2)]."""
+    L = _check_lattice(s)
+    rec = np.zeros(record_len(L), dtype=np.int64)
+    lib().orc_record(L, _p(s, ctypes.c_int8), t, _p(rec, ctypes.c_int64))
+    return rec
+
+
+def derived(L: int, rec: np.ndarray, c: float = 0.5, connected: bool = False) -> np.ndarray:
+    """[e, m, l_E, l_C] from one record (double precision)."""
+    rec = np.ascontiguousarray(rec, dtype=np.int64)
+    if rec.size != record_len(L):
+        raise ValueError("record length does not match L")
+    out = np.zeros(4, dtype=np.float64)
+    lib().orc_derived(L, _p(rec, ctypes.c_int64), c, int(bool(connected)), _p(out, ctypes.c_double))
+    return out
+
+
+def run(L: int, seed: int, replica: int, times, rule: int = TIE_GLAUBER, keep_spins: bool = False):
+    """Quench one replica and record at t = 0 and at every t in ``times`` (increasing).
+
+    Returns (records [len(times)+1, record_len], spins or None)."""
+    S = (seed + replica) % 2**64
+    s = init(L, seed, replica)
+    recs = [record(s, 0)]
+    spins = [s.copy()] if keep_spins else None
+    t = 0
+    for tk in times:
+        sweeps(s, t, tk - t, S, rule)
+        t = tk
+        recs.append(record(s, t))
+        if keep_spins:
+            spins.append(s.copy())
+    return np.stack(recs), spins

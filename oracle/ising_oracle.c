@@ -1,0 +1,275 @@
+/*
+ * CPU oracle for the zero-temperature checkerboard quench of the d=3 Ising model
+ * (Gessert, Christiansen, Janke, "Superdiffusion-like behavior in zero-temperature
+ * coarsening of the d=3 Ising model", arXiv:2305.12161).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, plain reference that the CUDA
+ * library is checked against.  Only tests/, __graft_entry__.smoke() and bench.py's
+ * cpu_baseline / --impl reference legs may load it.  It shares no code, header,
+ * table or helper with the CUDA library: everything below is written out from the
+ * paper's definitions and from the published Philox4x32-10 generator.
+ *
+ * Representation: one signed byte per spin, s in {-1,+1}, site (x,y,z) in [0,L)^3 with
+ * periodic boundaries, linear index i = x + L*(y + L*z) (64-bit: N = 2^33 at L = 2048).
+ *
+ * Every function is pinned by tests in tests/test_oracle_*.py (closed forms, fixed
+ * points, brute-force recounts, known-answer vectors); see the per-function notes.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_TIE_GLAUBER 0 /* Eq. (6): a zero-energy flip is accepted with probability 1/2 */
+#define ORC_TIE_ALWAYS 1  /* T->0 limit of Metropolis, min(1, e^0) = 1 (Supp. Methods I B) */
+#define ORC_TIE_NEVER 2   /* zero-energy flips rejected */
+
+/* Host threads used by the OpenMP loops below (1 when built without OpenMP). */
+int orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
+/* ------------------------------------------------------------------------------ */
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11, "Parallel random numbers: as easy
+ * as 1, 2, 3").  A 4x32-bit counter and a 2x32-bit key; ten rounds.  Each round
+ * multiplies counter words 0 and 2 by the two round multipliers into 64-bit products,
+ * recombines hi/lo halves with words 1 and 3 and the round key, and then the key is
+ * bumped by the two Weyl constants (golden ratio and sqrt(3)-1 in 32-bit fixed point).
+ * Pinned by the published known-answer vectors (tests/golden/philox4x32_10_kat.txt)
+ * and by an independent library implementation. */
+#define PHILOX_M0 0xD2511F53u
+#define PHILOX_M1 0xCD9E8D57u
+#define PHILOX_W0 0x9E3779B9u
+#define PHILOX_W1 0xBB67AE85u
+
+void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int round = 0; round < 10; ++round) {
+        uint64_t p0 = (uint64_t)PHILOX_M0 * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)PHILOX_M1 * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+        if (round < 9) { k0 += PHILOX_W0; k1 += PHILOX_W1; }
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* ------------------------------------------------------------------------------ */
+/* Random-bit addressing.  The paper names no generator and no mapping from random
+ * numbers to sites; this library fixes one so that every run is reproducible:
+ *   - a site (x,y,z) of sublattice q = (x+y+z) mod 2 gets the compressed index
+ *       h = (x >> 1) + (L/2) * (y + L*z)            in [0, N/2),
+ *     its 32-bit word w = h >> 5 and its bit j = h & 31;
+ *   - key = (lo32(S), hi32(S)) with S = seed + replica (mod 2^64);
+ *   - counter = (w >> 2, t, phase, 0), phase = q for the update of sweep t (0-based),
+ *     phase = 2 + q for the T = infinity initial state (t = 0);
+ *   - the bit is bit j of output word (w & 3). */
+int orc_rng_bit(uint64_t S, uint32_t t, uint32_t phase, int64_t h)
+{
+    int64_t w = h >> 5;
+    int j = (int)(h & 31);
+    uint32_t ctr[4] = {(uint32_t)(w >> 2), t, phase, 0u};
+    uint32_t key[2] = {(uint32_t)(S & 0xffffffffu), (uint32_t)(S >> 32)};
+    uint32_t o[4];
+    orc_philox4x32_10(ctr, key, o);
+    return (int)((o[w & 3] >> j) & 1u);
+}
+
+static inline int64_t site(int64_t L, int64_t x, int64_t y, int64_t z)
+{
+    return x + L * (y + L * z);
+}
+
+static inline int64_t wrap(int64_t a, int64_t L) { return ((a % L) + L) % L; }
+
+static inline int64_t compressed_index(int64_t L, int64_t x, int64_t y, int64_t z)
+{
+    return (x >> 1) + (L / 2) * (y + L * z);
+}
+
+/* ------------------------------------------------------------------------------ */
+/* T = infinity initial state (Results and Discussion: random spin configurations with
+ * m ~ 0): every spin is +1 or -1 independently with probability 1/2, the bit drawn
+ * with phase 2 + q at t = 0. */
+void orc_init(int L_, uint64_t S, int8_t *s)
+{
+    const int64_t L = L_;
+#pragma omp parallel for schedule(static)
+    for (int64_t z = 0; z < L; ++z)
+        for (int64_t y = 0; y < L; ++y)
+            for (int64_t x = 0; x < L; ++x) {
+                int q = (int)((x + y + z) & 1);
+                int b = orc_rng_bit(S, 0u, (uint32_t)(2 + q), compressed_index(L, x, y, z));
+                s[site(L, x, y, z)] = b ? (int8_t)1 : (int8_t)-1;
+            }
+}
+
+/* ------------------------------------------------------------------------------ */
+/* One half-sweep of the checkerboard update (Methods, "Checkerboard update"): every
+ * site of sublattice q (sites with (x+y+z) mod 2 == q; the 3-d generalisation of the
+ * checkerboard figure) is proposed once, all of them at the same time.  Their six
+ * nearest neighbours all lie on the other sublattice, so every proposal sees the
+ * neighbour values from before this half-sweep.
+ *
+ * Acceptance is the T -> 0 Glauber rule, Eq. (6): with H = -sum_<ij> s_i s_j (J = 1),
+ * flipping s_i changes the energy by dE = 2 s_i sum_nn s_j = 2 s_i (2u - 6), u = number
+ * of up neighbours.  dE < 0 -> flip, dE > 0 -> keep, dE = 0 (u = 3) -> flip with
+ * probability 1/2, i.e. when the site's random bit is 1 (or per the rule flag).
+ * Therefore the new spin is up for u >= 4 and down for u <= 2.
+ *
+ * Returns the number of flips; *dB receives the change of the broken-bond count B
+ * accumulated flip by flip (a flipped site with a aligned neighbours before the flip
+ * changes B by 2a - 6), *dM the change of the magnetisation. */
+int64_t orc_half_sweep(int L_, int8_t *s, int q, uint32_t t, uint64_t S, int rule,
+                       int64_t *dB, int64_t *dM)
+{
+    const int64_t L = L_;
+    int64_t flips = 0, db = 0, dm = 0;
+#pragma omp parallel for schedule(static) reduction(+ : flips, db, dm)
+    for (int64_t z = 0; z < L; ++z)
+        for (int64_t y = 0; y < L; ++y)
+            for (int64_t x = 0; x < L; ++x) {
+                if (((x + y + z) & 1) != q) continue;
+                int8_t nb[6] = {
+                    s[site(L, wrap(x + 1, L), y, z)], s[site(L, wrap(x - 1, L), y, z)],
+                    s[site(L, x, wrap(y + 1, L), z)], s[site(L, x, wrap(y - 1, L), z)],
+                    s[site(L, x, y, wrap(z + 1, L))], s[site(L, x, y, wrap(z - 1, L))]};
+                int u = 0;
+                for (int k = 0; k < 6; ++k) u += (nb[k] == 1);
+                int8_t old = s[site(L, x, y, z)];
+                int8_t nw;
+                if (u >= 4) {
+                    nw = 1;
+                } else if (u <= 2) {
+                    nw = -1;
+                } else if (rule == ORC_TIE_ALWAYS) {
+                    nw = (int8_t)-old;
+                } else if (rule == ORC_TIE_NEVER) {
+                    nw = old;
+                } else {
+                    int r = orc_rng_bit(S, t, (uint32_t)q, compressed_index(L, x, y, z));
+                    nw = r ? (int8_t)-old : old;
+                }
+                if (nw != old) {
+                    int aligned = 0;
+                    for (int k = 0; k < 6; ++k) aligned += (nb[k] == old);
+                    flips += 1;
+                    db += 2 * aligned - 6;
+                    dm += (int64_t)nw - (int64_t)old;
+                    s[site(L, x, y, z)] = nw;
+                }
+            }
+    if (dB) *dB = db;
+    if (dM) *dM = dm;
+    return flips;
+}
+
+/* n Monte Carlo sweeps starting at completed-sweep count t0.  One MCS (Methods,
+ * "Random-site-flip update": N proposals) is the red (q = 0) half-sweep followed by
+ * the blue (q = 1) half-sweep, both with the sweep's 0-based index as counter word. */
+void orc_sweeps(int L, int8_t *s, uint32_t t0, int64_t n, uint64_t S, int rule)
+{
+    for (int64_t k = 0; k < n; ++k) {
+        uint32_t t = t0 + (uint32_t)k;
+        orc_half_sweep(L, s, 0, t, S, rule, NULL, NULL);
+        orc_half_sweep(L, s, 1, t, S, rule, NULL, NULL);
+    }
+}
+
+/* ------------------------------------------------------------------------------ */
+/* Integer observables of one configuration, written as a record
+ *   rec[0] = t, rec[1] = M = sum_i s_i, rec[2] = B = number of unequal nearest-
+ *   neighbour pairs, then D_x(r), D_y(r), D_z(r) for r = 0..L/2, with
+ *   D_a(r) = #{ i : s_i != s_(i + r e_a) }.
+ * The spin-spin sum of Eq. (2) along axis a follows as sum_i s_i s_(i+r e_a) =
+ * N - 2 D_a(r); the energy of H = -sum_<ij> s_i s_j is E = -(3N - 2B). */
+int64_t orc_record_len(int L) { return 3 + 3 * (int64_t)(L / 2 + 1); }
+
+void orc_record(int L_, const int8_t *s, int64_t t, int64_t *rec)
+{
+    const int64_t L = L_;
+    const int64_t R = L / 2;
+    int64_t M = 0, B = 0;
+#pragma omp parallel for schedule(static) reduction(+ : M, B)
+    for (int64_t z = 0; z < L; ++z)
+        for (int64_t y = 0; y < L; ++y)
+            for (int64_t x = 0; x < L; ++x) {
+                int8_t v = s[site(L, x, y, z)];
+                M += v;
+                B += (v != s[site(L, wrap(x + 1, L), y, z)]);
+                B += (v != s[site(L, x, wrap(y + 1, L), z)]);
+                B += (v != s[site(L, x, y, wrap(z + 1, L))]);
+            }
+    rec[0] = t;
+    rec[1] = M;
+    rec[2] = B;
+    int64_t *Dx = rec + 3, *Dy = rec + 3 + (R + 1), *Dz = rec + 3 + 2 * (R + 1);
+    for (int64_t r = 0; r <= R; ++r) {
+        int64_t dx = 0, dy = 0, dz = 0;
+#pragma omp parallel for schedule(static) reduction(+ : dx, dy, dz)
+        for (int64_t z = 0; z < L; ++z)
+            for (int64_t y = 0; y < L; ++y)
+                for (int64_t x = 0; x < L; ++x) {
+                    int8_t v = s[site(L, x, y, z)];
+                    dx += (v != s[site(L, wrap(x + r, L), y, z)]);
+                    dy += (v != s[site(L, x, wrap(y + r, L), z)]);
+                    dz += (v != s[site(L, x, y, wrap(z + r, L))]);
+                }
+        Dx[r] = dx;
+        Dy[r] = dy;
+        Dz[r] = dz;
+    }
+}
+
+/* ------------------------------------------------------------------------------ */
+/* Quantities derived from one record (double precision):
+ *   out[0] = e   = E/N = -3 + 2B/N          (energy per spin)
+ *   out[1] = m   = M/N                      (magnetisation per spin)
+ *   out[2] = l_E = N/B = 2/(e - e0), e0 = -3 (length from the excess energy; +inf if B=0)
+ *   out[3] = l_C: C(r) = G(r)/(3N) with G(r) = sum_a (N - 2 D_a(r)) (minus m^2 when
+ *            `connected`, the second term of Eq. (2) taken per sample); l_C is the
+ *            intersection of C with the constant c (Results: "intersection of C(r,t)
+ *            with a constant value of c = 0.5"), linearly interpolated at the first r0
+ *            with C(r0) >= c > C(r0+1); NaN when C does not cross c for r <= L/2. */
+void orc_derived(int L_, const int64_t *rec, double c, int connected, double *out)
+{
+    const int64_t L = L_;
+    const int64_t R = L / 2;
+    const double N = (double)L * (double)L * (double)L;
+    const int64_t M = rec[1], B = rec[2];
+    const int64_t *Dx = rec + 3, *Dy = rec + 3 + (R + 1), *Dz = rec + 3 + 2 * (R + 1);
+    double m = (double)M / N;
+    out[0] = -3.0 + 2.0 * (double)B / N;
+    out[1] = m;
+    out[2] = (B == 0) ? INFINITY : N / (double)B;
+    double lc = NAN;
+    double sub = connected ? m * m : 0.0;
+    for (int64_t r = 0; r < R; ++r) {
+        double g0 = (N - 2.0 * (double)Dx[r]) + (N - 2.0 * (double)Dy[r]) + (N - 2.0 * (double)Dz[r]);
+        double g1 = (N - 2.0 * (double)Dx[r + 1]) + (N - 2.0 * (double)Dy[r + 1]) +
+                    (N - 2.0 * (double)Dz[r + 1]);
+        double c0 = g0 / (3.0 * N) - sub;
+        double c1 = g1 / (3.0 * N) - sub;
+        if (c0 >= c && c > c1) {
+            lc = (double)r + (c0 - c) / (c0 - c1);
+            break;
+        }
+    }
+    out[3] = lc;
+}
