@@ -1,0 +1,322 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the zero-temperature checkerboard quench on GB300.
+
+Workload (one step = one pass of the whole hot path over a 2048^3 lattice):
+  leg (i):  T = infinity Philox start (seed 1), 1000 MCS of the checkerboard T -> 0
+            Glauber dynamics, observables (M, B, D_a(r) for r = 0..1024, and e, m, l_E,
+            l_C) at K log-spaced times;
+  leg (ii): the configuration evolved to t = 10^4 MCS (sparse interfaces; prepared once,
+            untimed, kept in HBM), 1000 further MCS, observables at K log-spaced times.
+Metric: spin updates per ns over the whole step (2 x 1000 x 2048^3 updates).
+
+`value` runs with every input already in HBM (checkpoint copied device-to-device,
+records written to device buffers).  `e2e` runs the same step through the C ABI with
+host buffers: the checkpoint is copied from pinned host memory and every record is
+read back to the host, inside the timed region.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank runs its own independent lattice (replicas only; no exchange).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "spin updates/ns & % HBM roofline at L=2048; batched vs plain form on one GB300"
+UNIT = "spin updates/ns"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "src": "measured", "sm_max_mhz": float(d.get("sm_max_mhz", 2070.0))}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "src": "fallback", "sm_max_mhz": 2070.0}
+
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(sample_L: int = 1024, mcs: int = 2) -> dict:
+    """The oracle as it stands, on this host's cores, on a bounded sample."""
+    import oracle
+    cores = oracle.set_threads(os.cpu_count() or 1)
+    s = oracle.init(sample_L, 1)
+    t0 = time.perf_counter()
+    oracle.sweeps(s, 0, mcs, 1, oracle.TIE_GLAUBER)
+    dt = time.perf_counter() - t0
+    return {"value": mcs * sample_L**3 / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{mcs} MCS of one {sample_L}^3 lattice from the T=inf start (sweeps only, "
+                      f"no correlation pass), {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    cores = oracle.set_threads(os.cpu_count() or 1)
+    L, mcs = args.ref_L, 1
+    s = oracle.init(L, 1)
+    for _ in range(args.warmup):
+        oracle.sweeps(s, 0, mcs, 1, oracle.TIE_GLAUBER)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        oracle.sweeps(s, k * mcs, mcs, 1, oracle.TIE_GLAUBER)
+    dt = time.perf_counter() - t0
+    v = args.steps * mcs * L**3 / dt / 1e9
+    sample = f"each step: {mcs} MCS of one {L}^3 lattice (oracle sweeps only)"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int8", "data": "synthetic",
+        "config": {"workload": "L=2048 quench legs (oracle sample)", "L": L, "parallelism": "host threads"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--L", type=int, default=2048)
+    ap.add_argument("--mcs", type=int, default=1000)
+    ap.add_argument("--t-checkpoint", type=int, default=10_000)
+    ap.add_argument("--K", type=int, default=8, help="measured times per leg")
+    ap.add_argument("--ref-L", type=int, default=1024)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline()  # before any GPU work
+
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    from paper_2305_12161_gb300 import inputs, ising
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    if dist:
+        dist.barrier()
+
+    L, MCS, TCK, K = args.L, args.mcs, args.t_checkpoint, args.K
+    N = L**3
+    seed = 1 + 1000 * rank
+    stream = torch.cuda.Stream()
+    q = ising.Ising(L, replicas=1, seed=seed, stream=stream)
+    RL = q.record_len
+    offsets = inputs.log_schedule(MCS, K)
+    nwords = ising.ising_packed_words(L)
+
+    # leg (ii) input: the state at t = 10^4, prepared once (untimed)
+    q.sweep(TCK)
+    ck_dev = torch.empty(nwords, dtype=torch.int32, device="cuda")
+    q.get_packed(0, out=ck_dev, device=True)
+    ck_host = torch.empty(nwords, dtype=torch.int32, pin_memory=True)
+    q.sync()
+    ck_host.copy_(ck_dev.cpu())
+    ck_host_np = ck_host.numpy().view(np.uint32)
+    rec_dev = torch.empty((2, K, RL), dtype=torch.int64, device="cuda")
+    der_dev = torch.empty((2, K, 4), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+
+    sweep_events, meas_events = [], []
+
+    def ev():
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(stream)
+        return e
+
+    def step(e2e: bool, timing: bool):
+        outs = []
+        for leg in (0, 1):
+            if leg == 0:
+                q.reinit(seed)
+                t0 = 0
+            else:
+                if e2e:
+                    q.set_packed(ck_host_np, 0)
+                else:
+                    q.set_packed(ck_dev, 0, device=True)
+                q.t = TCK
+                t0 = TCK
+            t = t0
+            for k, off in enumerate(offsets):
+                a = ev() if timing else None
+                q.sweep(t0 + off - t)
+                b = ev() if timing else None
+                t = t0 + off
+                if e2e:
+                    outs.append(q.measure_ex(c=0.5))
+                else:
+                    q.measure_device(rec_dev[leg, k], der_dev[leg, k], c=0.5)
+                c = ev() if timing else None
+                if timing:
+                    sweep_events.append((a, b, 2 * (off - (offsets[k - 1] if k else 0))))
+                    meas_events.append((b, c))
+        return outs
+
+    def timed(e2e: bool, n: int):
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        l0 = q.launch_count()
+        start = ev()
+        for _ in range(n):
+            step(e2e, timing=not e2e)
+        end = ev()
+        torch.cuda.synchronize()
+        ms = start.elapsed_time(end)
+        if dist:
+            tt = torch.tensor([ms], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            ms = float(tt.item())
+        return ms, q.launch_count() - l0
+
+    for _ in range(args.warmup):
+        step(False, timing=False)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms, launches = timed(False, args.steps)
+    clk = clocks.stop()
+    e2e_ms = None
+    if not args.no_e2e:
+        step(True, timing=False)  # warm the host path
+        e2e_ms, _ = timed(True, args.steps)
+
+    updates_per_step = 2 * MCS * N
+    value = world * updates_per_step * args.steps / (ms * 1e-3) / 1e9
+
+    # per-kernel live timings (CUDA events on the launching stream, inside the timed region)
+    sweep_ms = sum(a.elapsed_time(b) for a, b, _ in sweep_events)
+    sweep_launches = sum(n for _, _, n in sweep_events)
+    meas_ms = sum(a.elapsed_time(b) for a, b in meas_events)
+    pk = _peaks()
+    bytes_per_launch = 3 * (N // 2) / 8  # read q, read q-bar, write q: 1 bit each per site
+    sweep_avg_s = sweep_ms * 1e-3 / sweep_launches
+    sweep_gbs = bytes_per_launch / sweep_avg_s / 1e9
+    # correlation pass: XOR+popc word operations, 3 axes x L/2 lags x N/32 words
+    corr_ops = 3 * (L // 2) * (N // 32)
+    n_meas = len(meas_events)
+    meas_avg_s = meas_ms * 1e-3 / n_meas
+    popc_peak = 152 * 16 * pk["sm_max_mhz"] * 1e6 / 1e12  # T popc/s: 16 per SM per clock
+    corr_tops = corr_ops / meas_avg_s / 1e12
+    roof_sweep = {"kernel": "k_sweep_zmarch (half-sweep)", "bound": "hbm", "achieved": sweep_gbs,
+                  "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": sweep_gbs / pk["hbm_gbs"], "traffic": None,
+                  "peak_src": pk["src"], "avg_launch_ms": sweep_avg_s * 1e3, "bytes_per_launch": bytes_per_launch,
+                  "updates_per_ns": (N // 2) / sweep_avg_s / 1e9}
+    roof_corr = {"kernel": "k_corr + k_mb (one measurement)", "bound": "alu", "achieved": corr_tops,
+                 "peak": popc_peak, "unit": "Tpopc/s", "frac": corr_tops / popc_peak, "traffic": None,
+                 "avg_launch_ms": meas_avg_s * 1e3, "ops_per_launch": corr_ops}
+    roof = roof_sweep if sweep_ms >= meas_ms else roof_corr
+    e2e = None
+    if e2e_ms is not None:
+        d2h = 2 * K * (RL * 8 + 4 * 8)
+        e2e = {"value": world * updates_per_step * args.steps / (e2e_ms * 1e-3) / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": nwords * 4, "d2h_bytes_per_step": d2h}
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32 (1-bit spins, integer logic)", "data": "synthetic",
+            "config": {"workload": f"L={L} single lattice: T=inf start + {MCS} MCS, and t={TCK} state + {MCS} MCS; "
+                                   f"M, B, D_a(r<=L/2), e, m, l_E, l_C at {K} log-spaced times per leg",
+                       "L": L, "mcs_per_leg": MCS, "legs": 2, "measurements_per_leg": K, "form": "packed",
+                       "l2": "inputs larger than L2 (1 GiB packed lattice > 129 MB)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roof, "roofline_sweep": roof_sweep, "roofline_measure": roof_corr,
+            "breakdown_ms_per_step": {"sweeps": sweep_ms / args.steps, "measurements": meas_ms / args.steps},
+            "sweep_only_updates_per_ns": world * (N // 2) / sweep_avg_s / 1e9,
+            "clocks": clk, "e2e": e2e, "gpu_launches": launches,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(out))
+    q.destroy()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

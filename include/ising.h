@@ -1,0 +1,168 @@
+/*
+ * ising.h — C ABI of the GB300 zero-temperature checkerboard quench library.
+ *
+ * The library simulates the quench studied in Gessert, Christiansen, Janke,
+ * "Superdiffusion-like behavior in zero-temperature coarsening of the d=3 Ising model"
+ * (arXiv:2305.12161): a periodic simple-cubic L^3 nearest-neighbour Ising model
+ * (H = -sum_<ij> s_i s_j) started from an infinite-temperature configuration and
+ * evolved with single-spin flips under the T -> 0 Glauber acceptance (Eq. 6: dE < 0
+ * always, dE > 0 never, dE = 0 with probability 1/2), proposals ordered by the
+ * checkerboard decomposition (Methods, "Checkerboard update": all red sites, x+y+z
+ * even, at once, then all blue sites).  One Monte Carlo sweep (MCS) is both halves.
+ * Observables are the integer magnetisation, broken-bond count and the axis
+ * correlation sums behind Eq. (2).
+ *
+ * Conventions shared by every entry point
+ *   - Every function returns an ising_status (0 = ISING_OK, negative = error) unless
+ *     stated otherwise.  Nothing is thrown across the ABI.
+ *   - A context (ising_ctx) owns all device memory of its replicas.  The caller owns
+ *     every host buffer, every device buffer it passes in, and the CUDA stream.
+ *   - Work is enqueued on the context's stream (a cudaStream_t given at creation, or a
+ *     stream the library creates).  Functions that write host memory synchronise that
+ *     stream before returning; the others return once the work is enqueued.
+ *   - A CUDA error or a device-side timeout poisons the context: every later call
+ *     except ising_destroy / ising_strerror / ising_last_error returns ISING_EPOISONED.
+ *   - Site (x,y,z), 0 <= x,y,z < L, has linear index i = x + L*(y + L*z) (64-bit).
+ *     Sublattice q = (x+y+z) mod 2; q = 0 ("red") is updated first in every sweep.
+ *   - Randomness: Philox4x32-10 (Salmon et al., SC'11).  The bit of a site of
+ *     sublattice q is bit (h & 31) of output word ((h >> 5) & 3) of
+ *     Philox(counter = (h >> 7, t, phase, 0), key = (lo32(S), hi32(S))) with
+ *     h = (x >> 1) + (L/2)*(y + L*z), S = seed + replica (mod 2^64), phase = q for the
+ *     zero-energy decision of sweep t (0-based), phase = 2 + q for the initial state.
+ *     A run is therefore reproducible bit for bit and independent of launch shapes.
+ */
+#ifndef ISING_H
+#define ISING_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ising_ctx ising_ctx;
+
+typedef enum {
+    ISING_OK = 0,
+    ISING_EINVAL = -1,    /* bad argument (size, pointer, replica index, flag) */
+    ISING_ENOMEM = -2,    /* device or host allocation failed */
+    ISING_ECUDA = -3,     /* a CUDA call failed; the context is poisoned */
+    ISING_ETIMEOUT = -4,  /* a bounded device-side wait gave up; the context is poisoned */
+    ISING_EBUSY = -5,     /* resource in use (e.g. a batch already running) */
+    ISING_EPOISONED = -6  /* an earlier error poisoned this context */
+} ising_status;
+
+/* Zero-energy (u = 3 up neighbours) rule.  GLAUBER is the paper's (Eq. 6). */
+typedef enum {
+    ISING_TIE_GLAUBER = 0, /* flip iff the site's Philox bit is 1 (probability 1/2) */
+    ISING_TIE_ALWAYS = 1,  /* always flip: T -> 0 limit of Metropolis, min(1, e^0) */
+    ISING_TIE_NEVER = 2    /* never flip */
+} ising_tie;
+
+/* Storage form.  PACKED: 1 bit per spin, each sublattice in its own array (the fast
+ * form).  PLAIN: one signed byte per spin, one kernel launch per lattice and
+ * half-sweep (the comparison form).  Both produce identical spins and records. */
+typedef enum { ISING_FORM_PACKED = 0, ISING_FORM_PLAIN = 1 } ising_form;
+
+typedef struct {
+    int tie;        /* ising_tie */
+    int form;       /* ising_form */
+    void *stream;   /* cudaStream_t to enqueue on; NULL: the library creates one */
+    int device;     /* CUDA device ordinal; -1: the current device */
+    int variant;    /* packed sweep kernel variant, 0 = automatic (see ising_variants) */
+    int tile_y;     /* packed z-marching variant: rows per tile (0 = automatic) */
+    int tile_z;     /* packed z-marching variant: planes per tile (0 = automatic) */
+} ising_opts;
+
+/* Fill *opts with the defaults: GLAUBER, PACKED, own stream, current device, auto. */
+void ising_default_opts(ising_opts *opts);
+
+/* Create R = `replicas` independent lattices of linear size L, replica r seeded with
+ * S = seed + r, each in its T = infinity initial state (t = 0; Results and Discussion:
+ * random configurations with m ~ 0, drawn here i.i.d. with probability 1/2).
+ * L must be even and >= 4; the PACKED form additionally needs L a multiple of 64 or
+ * L in {4, 8, 16, 32}.  On success *out receives the context; on error *out = NULL. */
+int ising_create(ising_ctx **out, int L, int replicas, uint64_t seed);
+int ising_create_ex(ising_ctx **out, int L, int replicas, uint64_t seed, const ising_opts *opts);
+
+/* Redraw every replica's T = infinity initial state for a new seed (replica r uses
+ * seed + r) and reset t to 0, reusing the context's memory.  Enqueued, no sync. */
+int ising_reinit(ising_ctx *ctx, uint64_t seed);
+
+/* Enqueue n_mcs >= 0 Monte Carlo sweeps on every replica (each sweep: red half-sweep,
+ * then blue half-sweep; Methods, "Checkerboard update").  Advances the context's
+ * time t by n_mcs.  Returns once the work is enqueued. */
+int ising_sweep(ising_ctx *ctx, int64_t n_mcs);
+
+/* Number of int64 values of one replica's record:
+ *   [t, M, B, D_x(0..L/2), D_y(0..L/2), D_z(0..L/2)]  -> 3 + 3*(L/2 + 1),
+ * t = completed MCS, M = sum_i s_i, B = number of unequal nearest-neighbour pairs
+ * (E = -(3N - 2B)), D_a(r) = #{ i : s_i != s_(i + r e_a) }.  Returns -1 for bad L. */
+int64_t ising_record_len(int L);
+
+/* Measure every replica and write replicas * ising_record_len(L) int64 values to the
+ * HOST buffer `out` (replica-major).  Synchronises the context's stream. */
+int ising_measure(ising_ctx *ctx, int64_t *out);
+
+/* Flags of ising_measure_ex. */
+#define ISING_MEAS_DEVICE 1u    /* rec / derived are device pointers; do not synchronise */
+#define ISING_MEAS_CONNECTED 2u /* derived l_C uses C(r) - m^2 (second term of Eq. 2) */
+#define ISING_MEAS_NO_CORR 4u   /* skip D_a(r) (they are written as -1): energy and m only */
+
+/* Measure into `rec` (replicas * record_len int64, may be NULL) and, if `derived` is
+ * not NULL, write per replica 4 doubles [e, m, l_E, l_C]:
+ *   e = -3 + 2B/N, m = M/N, l_E = N/B (+inf when B = 0),
+ *   l_C = first intersection of C(r) = sum_a (N - 2 D_a(r)) / (3N) with the constant
+ *   c (Results: c = 0.5), linearly interpolated; NaN if C does not cross c, r <= L/2.
+ * Without ISING_MEAS_DEVICE both pointers are host memory and the call synchronises. */
+int ising_measure_ex(ising_ctx *ctx, int64_t *rec, double *derived, double c, unsigned flags);
+
+/* Copy one replica's spins to / from a HOST int8 buffer of N = L^3 values (+1 / -1)
+ * indexed x + L*(y + L*z).  ising_set_spins rejects values other than +-1 with
+ * ISING_EINVAL (checked on the host before anything is copied).  Both synchronise. */
+int ising_get_spins(ising_ctx *ctx, int replica, int8_t *host_out);
+int ising_set_spins(ising_ctx *ctx, int replica, const int8_t *host_in);
+
+/* Flags of the packed-state calls. */
+#define ISING_PTR_DEVICE 1u /* the buffer is device memory; no synchronisation */
+
+/* Number of uint32 words of one replica's packed state (2 * ceil(N/64) style, see
+ * below); -1 for bad L.  Layout: sublattice 0 then sublattice 1; within a sublattice,
+ * bit j of word w is the site with compressed index h = 32*w + j (1 = up) for
+ * L a multiple of 64; for L < 64 each row (y,z) has its own word holding its L/2 sites
+ * in bits 0..L/2-1.  This is the checkpoint format: with (seed, t) it resumes a run
+ * bit for bit. */
+int64_t ising_packed_words(int L);
+int ising_get_packed(ising_ctx *ctx, int replica, uint32_t *words, unsigned flags);
+int ising_set_packed(ising_ctx *ctx, int replica, const uint32_t *words, unsigned flags);
+
+/* Completed-sweep counter t shared by all replicas of the context. */
+int ising_get_time(ising_ctx *ctx, int64_t *t);
+int ising_set_time(ising_ctx *ctx, int64_t t);
+
+/* Block until the context's stream is idle; reports asynchronous errors. */
+int ising_sync(ising_ctx *ctx);
+
+/* Release the context and its device memory.  NULL-safe.  Always returns ISING_OK for
+ * a valid or NULL pointer. */
+int ising_destroy(ising_ctx *ctx);
+
+/* Static message for a status code. */
+const char *ising_strerror(int status);
+
+/* Detail of the last error recorded on the context (empty string if none). */
+const char *ising_last_error(const ising_ctx *ctx);
+
+/* Number of kernel launches this context has enqueued so far (diagnostics). */
+int64_t ising_launch_count(const ising_ctx *ctx);
+
+/* Packed sweep kernel variants: fills up to `cap` ids into `ids`, returns the number.
+ * Every variant produces bit-identical results; they differ in speed only. */
+int ising_variants(int *ids, int cap);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ISING_H */

@@ -72,6 +72,13 @@ def lib() -> ctypes.CDLL:
             L.orc_record_len.restype = ctypes.c_int64
             L.orc_record.argtypes = [ctypes.c_int, i8p, ctypes.c_int64, i64p]
             L.orc_record.restype = None
+            L.orc_update_sites.argtypes = [ctypes.c_int, i8p, ctypes.c_int, ctypes.c_uint32, ctypes.c_uint64,
+                                           ctypes.c_int, i64p, ctypes.c_int64, i8p]
+            L.orc_update_sites.restype = None
+            L.orc_magnetisation_bonds.argtypes = [ctypes.c_int, i8p, i64p, i64p]
+            L.orc_magnetisation_bonds.restype = None
+            L.orc_corr_lag.argtypes = [ctypes.c_int, i8p, ctypes.c_int64, i64p]
+            L.orc_corr_lag.restype = None
             L.orc_derived.argtypes = [ctypes.c_int, i64p, ctypes.c_double, ctypes.c_int, f64p]
             L.orc_derived.restype = None
             _lib = L
@@ -141,6 +148,33 @@ def record(s: np.ndarray, t: int = 0) -> np.ndarray:
     rec = np.zeros(record_len(L), dtype=np.int64)
     lib().orc_record(L, _p(s, ctypes.c_int8), t, _p(rec, ctypes.c_int64))
     return rec
+
+
+def update_sites(s: np.ndarray, q: int, t: int, S: int, sites: np.ndarray, rule: int = TIE_GLAUBER) -> np.ndarray:
+    """New values the half-sweep (q, t) gives the listed sites (linear indices on q)."""
+    L = _check_lattice(s)
+    idx = np.ascontiguousarray(sites, dtype=np.int64)
+    out = np.empty(idx.size, dtype=np.int8)
+    lib().orc_update_sites(L, _p(s, ctypes.c_int8), q, t, S % 2**64, rule, _p(idx, ctypes.c_int64), idx.size,
+                           _p(out, ctypes.c_int8))
+    return out
+
+
+def magnetisation_bonds(s: np.ndarray):
+    """(M, B) of one configuration."""
+    L = _check_lattice(s)
+    M = ctypes.c_int64(0)
+    B = ctypes.c_int64(0)
+    lib().orc_magnetisation_bonds(L, _p(s, ctypes.c_int8), ctypes.byref(M), ctypes.byref(B))
+    return int(M.value), int(B.value)
+
+
+def corr_lag(s: np.ndarray, r: int) -> np.ndarray:
+    """[D_x(r), D_y(r), D_z(r)] of one configuration."""
+    L = _check_lattice(s)
+    out = np.zeros(3, dtype=np.int64)
+    lib().orc_corr_lag(L, _p(s, ctypes.c_int8), r, _p(out, ctypes.c_int64))
+    return out
 
 
 def derived(L: int, rec: np.ndarray, c: float = 0.5, connected: bool = False) -> np.ndarray:

@@ -136,6 +136,29 @@ void orc_init(int L_, uint64_t S, int8_t *s)
  * Returns the number of flips; *dB receives the change of the broken-bond count B
  * accumulated flip by flip (a flipped site with a aligned neighbours before the flip
  * changes B by 2a - 6), *dM the change of the magnetisation. */
+/* New value of site (x,y,z) of sublattice q under the rule above, reading its six
+ * neighbours from s; *aligned receives the number of neighbours equal to the old spin. */
+static int8_t site_new_value(int64_t L, const int8_t *s, int64_t x, int64_t y, int64_t z, int q, uint32_t t,
+                             uint64_t S, int rule, int *aligned)
+{
+    int8_t nb[6] = {
+        s[site(L, wrap(x + 1, L), y, z)], s[site(L, wrap(x - 1, L), y, z)],
+        s[site(L, x, wrap(y + 1, L), z)], s[site(L, x, wrap(y - 1, L), z)],
+        s[site(L, x, y, wrap(z + 1, L))], s[site(L, x, y, wrap(z - 1, L))]};
+    int u = 0;
+    for (int k = 0; k < 6; ++k) u += (nb[k] == 1);
+    int8_t old = s[site(L, x, y, z)];
+    int a = 0;
+    for (int k = 0; k < 6; ++k) a += (nb[k] == old);
+    if (aligned) *aligned = a;
+    if (u >= 4) return 1;
+    if (u <= 2) return -1;
+    if (rule == ORC_TIE_ALWAYS) return (int8_t)-old;
+    if (rule == ORC_TIE_NEVER) return old;
+    int r = orc_rng_bit(S, t, (uint32_t)q, compressed_index(L, x, y, z));
+    return r ? (int8_t)-old : old;
+}
+
 int64_t orc_half_sweep(int L_, int8_t *s, int q, uint32_t t, uint64_t S, int rule,
                        int64_t *dB, int64_t *dM)
 {
@@ -146,29 +169,10 @@ int64_t orc_half_sweep(int L_, int8_t *s, int q, uint32_t t, uint64_t S, int rul
         for (int64_t y = 0; y < L; ++y)
             for (int64_t x = 0; x < L; ++x) {
                 if (((x + y + z) & 1) != q) continue;
-                int8_t nb[6] = {
-                    s[site(L, wrap(x + 1, L), y, z)], s[site(L, wrap(x - 1, L), y, z)],
-                    s[site(L, x, wrap(y + 1, L), z)], s[site(L, x, wrap(y - 1, L), z)],
-                    s[site(L, x, y, wrap(z + 1, L))], s[site(L, x, y, wrap(z - 1, L))]};
-                int u = 0;
-                for (int k = 0; k < 6; ++k) u += (nb[k] == 1);
+                int aligned = 0;
                 int8_t old = s[site(L, x, y, z)];
-                int8_t nw;
-                if (u >= 4) {
-                    nw = 1;
-                } else if (u <= 2) {
-                    nw = -1;
-                } else if (rule == ORC_TIE_ALWAYS) {
-                    nw = (int8_t)-old;
-                } else if (rule == ORC_TIE_NEVER) {
-                    nw = old;
-                } else {
-                    int r = orc_rng_bit(S, t, (uint32_t)q, compressed_index(L, x, y, z));
-                    nw = r ? (int8_t)-old : old;
-                }
+                int8_t nw = site_new_value(L, s, x, y, z, q, t, S, rule, &aligned);
                 if (nw != old) {
-                    int aligned = 0;
-                    for (int k = 0; k < 6; ++k) aligned += (nb[k] == old);
                     flips += 1;
                     db += 2 * aligned - 6;
                     dm += (int64_t)nw - (int64_t)old;
@@ -178,6 +182,22 @@ int64_t orc_half_sweep(int L_, int8_t *s, int q, uint32_t t, uint64_t S, int rul
     if (dB) *dB = db;
     if (dM) *dM = dm;
     return flips;
+}
+
+/* The values that the half-sweep of sublattice q at sweep t would give the n listed
+ * sites (linear indices, each on sublattice q), without modifying s.  A site's update
+ * reads only the other sublattice, so this equals the full half-sweep at those sites;
+ * it lets lattices too large for a full oracle pass be checked site by site. */
+void orc_update_sites(int L_, const int8_t *s, int q, uint32_t t, uint64_t S, int rule,
+                      const int64_t *sites, int64_t n, int8_t *out)
+{
+    const int64_t L = L_;
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < n; ++k) {
+        int64_t i = sites[k];
+        int64_t x = i % L, y = (i / L) % L, z = i / (L * L);
+        out[k] = site_new_value(L, s, x, y, z, q, t, S, rule, NULL);
+    }
 }
 
 /* n Monte Carlo sweeps starting at completed-sweep count t0.  One MCS (Methods,
@@ -201,10 +221,10 @@ void orc_sweeps(int L, int8_t *s, uint32_t t0, int64_t n, uint64_t S, int rule)
  * N - 2 D_a(r); the energy of H = -sum_<ij> s_i s_j is E = -(3N - 2B). */
 int64_t orc_record_len(int L) { return 3 + 3 * (int64_t)(L / 2 + 1); }
 
-void orc_record(int L_, const int8_t *s, int64_t t, int64_t *rec)
+/* M and B of one configuration. */
+void orc_magnetisation_bonds(int L_, const int8_t *s, int64_t *M_out, int64_t *B_out)
 {
     const int64_t L = L_;
-    const int64_t R = L / 2;
     int64_t M = 0, B = 0;
 #pragma omp parallel for schedule(static) reduction(+ : M, B)
     for (int64_t z = 0; z < L; ++z)
@@ -216,24 +236,42 @@ void orc_record(int L_, const int8_t *s, int64_t t, int64_t *rec)
                 B += (v != s[site(L, x, wrap(y + 1, L), z)]);
                 B += (v != s[site(L, x, y, wrap(z + 1, L))]);
             }
+    *M_out = M;
+    *B_out = B;
+}
+
+/* D_x(r), D_y(r), D_z(r) for one distance r. */
+void orc_corr_lag(int L_, const int8_t *s, int64_t r, int64_t *D3)
+{
+    const int64_t L = L_;
+    int64_t dx = 0, dy = 0, dz = 0;
+#pragma omp parallel for schedule(static) reduction(+ : dx, dy, dz)
+    for (int64_t z = 0; z < L; ++z)
+        for (int64_t y = 0; y < L; ++y)
+            for (int64_t x = 0; x < L; ++x) {
+                int8_t v = s[site(L, x, y, z)];
+                dx += (v != s[site(L, wrap(x + r, L), y, z)]);
+                dy += (v != s[site(L, x, wrap(y + r, L), z)]);
+                dz += (v != s[site(L, x, y, wrap(z + r, L))]);
+            }
+    D3[0] = dx;
+    D3[1] = dy;
+    D3[2] = dz;
+}
+
+void orc_record(int L_, const int8_t *s, int64_t t, int64_t *rec)
+{
+    const int64_t L = L_;
+    const int64_t R = L / 2;
     rec[0] = t;
-    rec[1] = M;
-    rec[2] = B;
+    orc_magnetisation_bonds(L_, s, &rec[1], &rec[2]);
     int64_t *Dx = rec + 3, *Dy = rec + 3 + (R + 1), *Dz = rec + 3 + 2 * (R + 1);
     for (int64_t r = 0; r <= R; ++r) {
-        int64_t dx = 0, dy = 0, dz = 0;
-#pragma omp parallel for schedule(static) reduction(+ : dx, dy, dz)
-        for (int64_t z = 0; z < L; ++z)
-            for (int64_t y = 0; y < L; ++y)
-                for (int64_t x = 0; x < L; ++x) {
-                    int8_t v = s[site(L, x, y, z)];
-                    dx += (v != s[site(L, wrap(x + r, L), y, z)]);
-                    dy += (v != s[site(L, x, wrap(y + r, L), z)]);
-                    dz += (v != s[site(L, x, y, wrap(z + r, L))]);
-                }
-        Dx[r] = dx;
-        Dy[r] = dy;
-        Dz[r] = dz;
+        int64_t D3[3];
+        orc_corr_lag(L_, s, r, D3);
+        Dx[r] = D3[0];
+        Dy[r] = D3[1];
+        Dz[r] = D3[2];
     }
 }
 

@@ -1,0 +1,165 @@
+// Device-side building blocks shared by the library's kernels: the lattice geometry of
+// the 1-bit sublattice store, Philox4x32-10, the random word of a storage word, and
+// the bit-sliced six-neighbour majority of the T -> 0 Glauber rule.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ising {
+
+enum Rule : int { TIE_GLAUBER = 0, TIE_ALWAYS = 1, TIE_NEVER = 2 };
+
+// Geometry of one lattice in the packed store.
+//   Sublattice q = (x+y+z) mod 2 holds the N/2 sites x = 2k + p, p = (y+z+q) mod 2,
+//   k = 0..L/2-1 of every row (y,z).  Row index row = y + L*z.
+//   L >= 64 (multiple of 64): a row is W = L/64 words of 32 bits, bit b of word kw is
+//   k = 32*kw + b, so storage word sw = row*W + kw is exactly compressed-index word
+//   h >> 5 of the sites it holds.
+//   L in {4,8,16,32}: a row is one word holding its RB = L/2 sites in bits 0..RB-1.
+struct Geom {
+    int L;
+    int W;        // words per row
+    int RB;       // valid bits per word (32, or L/2 for L < 64)
+    int64_t nw;   // words per sublattice = L*L*W
+};
+
+__host__ __device__ inline Geom make_geom(int L)
+{
+    Geom g;
+    g.L = L;
+    g.W = L >= 64 ? L / 64 : 1;
+    g.RB = L >= 64 ? 32 : L / 2;
+    g.nw = (int64_t)L * L * g.W;
+    return g;
+}
+
+__host__ __device__ inline uint32_t row_mask(int RB) { return RB >= 32 ? 0xffffffffu : ((1u << RB) - 1u); }
+
+// ---------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32->64-bit
+// products of counter words 0 and 2 with the round multipliers, the high halves mixed
+// into words 1 and 3 with the round key; the key advances by the Weyl constants.
+struct U4 {
+    uint32_t x, y, z, w;
+};
+
+__device__ __forceinline__ U4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                            uint32_t k0, uint32_t k1)
+{
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+    for (int i = 0; i < 10; ++i) {
+        const uint32_t lo0 = M0 * c0, hi0 = __umulhi(M0, c0);
+        const uint32_t lo1 = M1 * c2, hi1 = __umulhi(M1, c2);
+        const uint32_t n0 = hi1 ^ c1 ^ k0;
+        const uint32_t n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+        k0 += W0;
+        k1 += W1;
+    }
+    return U4{c0, c1, c2, c3};
+}
+
+__device__ __forceinline__ uint32_t pick(const U4 &o, int i)
+{
+    return i == 0 ? o.x : (i == 1 ? o.y : (i == 2 ? o.z : o.w));
+}
+
+// Random bits of storage word sw (bit b = the bit of the word's site b) for `phase`
+// (q for the zero-energy decision of sweep t, 2+q for the initial state, t = 0).
+__device__ __forceinline__ uint32_t rng_word(const Geom &g, int64_t sw, uint32_t t, uint32_t phase,
+                                             uint64_t S)
+{
+    const uint32_t k0 = (uint32_t)S, k1 = (uint32_t)(S >> 32);
+    if (g.L >= 64) {
+        const U4 o = philox4x32_10((uint32_t)(sw >> 2), t, phase, 0u, k0, k1);
+        return pick(o, (int)(sw & 3));
+    }
+    const int64_t h0 = (int64_t)g.RB * sw;  // first compressed index of the row
+    const int64_t w = h0 >> 5;
+    const U4 o = philox4x32_10((uint32_t)(w >> 2), t, phase, 0u, k0, k1);
+    return (pick(o, (int)(w & 3)) >> (h0 & 31)) & row_mask(g.RB);
+}
+
+// ---------------------------------------------------------------------------------
+// Six-input bit-sliced counter: for each bit lane, u = number of set inputs among
+// a..f.  Returns ge4 = [u >= 4] and eq3 = [u == 3] lane masks.
+//   Two full adders give u = s1 + s2 + 2(c1 + c2); with a0 = s1^s2, a1 = s1&s2:
+//   u = a0 + 2(a1 + c1 + c2).  u >= 4 <=> a1 + c1 + c2 >= 2 (majority);
+//   u == 3 <=> a0 = 1 (then a1 = 0) and c1 + c2 = 1.
+__device__ __forceinline__ void count6(uint32_t a, uint32_t b, uint32_t c, uint32_t d, uint32_t e,
+                                       uint32_t f, uint32_t &ge4, uint32_t &eq3)
+{
+    const uint32_t s1 = a ^ b ^ c;
+    const uint32_t c1 = (a & b) | (c & (a ^ b));
+    const uint32_t s2 = d ^ e ^ f;
+    const uint32_t c2 = (d & e) | (f & (d ^ e));
+    const uint32_t a0 = s1 ^ s2;
+    const uint32_t a1 = s1 & s2;
+    ge4 = (a1 & c1) | (a1 & c2) | (c1 & c2);
+    eq3 = a0 & (c1 ^ c2);
+}
+
+// New spins of one word (T -> 0 Glauber, Eq. 6): up where u >= 4, down where u <= 2,
+// ties resolved by the rule: GLAUBER flips where the random bit is 1.
+template <int RULE>
+__device__ __forceinline__ uint32_t resolve(uint32_t s, uint32_t ge4, uint32_t eq3, uint32_t rnd)
+{
+    uint32_t tie;
+    if (RULE == TIE_GLAUBER)
+        tie = s ^ rnd;
+    else if (RULE == TIE_ALWAYS)
+        tie = ~s;
+    else
+        tie = s;
+    return ge4 | (eq3 & tie);
+}
+
+// Neighbour words of storage word sw of sublattice q, read from the other sublattice
+// array O.  X is the x-neighbour that is not at the same k (k-1 for p = 0, k+1 for
+// p = 1; the other x-neighbour is C itself), Ym/Yp/Zm/Zp are the rows y-1, y+1,
+// z-1, z+1 of O at the same word (their sites share x with ours).
+struct Nbrs {
+    uint32_t C, X, Ym, Yp, Zm, Zp;
+};
+
+__device__ __forceinline__ Nbrs load_nbrs(const uint32_t *__restrict__ O, const Geom &g, int64_t sw, int q)
+{
+    const int L = g.L, W = g.W;
+    const int64_t row = sw / W;
+    const int kw = (int)(sw - row * W);
+    const int y = (int)(row % L);
+    const int z = (int)(row / L);
+    const int p = (y + z + q) & 1;
+    Nbrs n;
+    n.C = __ldg(O + sw);
+    if (W >= 2) {
+        if (p == 0) {
+            const uint32_t e = __ldg(O + row * W + (kw == 0 ? W - 1 : kw - 1));
+            n.X = (n.C << 1) | (e >> 31);
+        } else {
+            const uint32_t e = __ldg(O + row * W + (kw == W - 1 ? 0 : kw + 1));
+            n.X = (n.C >> 1) | (e << 31);
+        }
+    } else {
+        const int RB = g.RB;
+        if (p == 0)
+            n.X = ((n.C << 1) | (n.C >> (RB - 1))) & row_mask(RB);
+        else
+            n.X = (n.C >> 1) | ((n.C & 1u) << (RB - 1));
+    }
+    const int ym = y == 0 ? L - 1 : y - 1, yp = y == L - 1 ? 0 : y + 1;
+    const int zm = z == 0 ? L - 1 : z - 1, zp = z == L - 1 ? 0 : z + 1;
+    n.Ym = __ldg(O + ((int64_t)z * L + ym) * W + kw);
+    n.Yp = __ldg(O + ((int64_t)z * L + yp) * W + kw);
+    n.Zm = __ldg(O + ((int64_t)zm * L + y) * W + kw);
+    n.Zp = __ldg(O + ((int64_t)zp * L + y) * W + kw);
+    return n;
+}
+
+}  // namespace ising

@@ -1,0 +1,422 @@
+// C ABI of the library (declared in include/ising.h): context lifecycle, argument
+// checks, error handling and dispatch to the kernels.  No kernel math lives here.
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/ising.h"
+#include "common.cuh"
+#include "kernels.h"
+
+using namespace ising;
+
+struct ising_ctx {
+    int L = 0, R = 0;
+    uint64_t seed = 0;
+    ising_opts opts{};
+    Geom g{};
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    uint32_t *lat = nullptr;     // packed store (PACKED form), or measurement copy (PLAIN form)
+    int8_t *plain = nullptr;     // PLAIN form lattice
+    int64_t *rec_dev = nullptr;  // R records
+    double *der_dev = nullptr;   // R x 4
+    int64_t t = 0;
+    int poisoned = 0;
+    int64_t launches = 0;
+    SweepConfig cfg{};
+    char err[256] = {0};
+};
+
+namespace {
+
+int fail(ising_ctx *c, int status, const char *fmt, ...)
+{
+    if (c) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(c->err, sizeof(c->err), fmt, ap);
+        va_end(ap);
+        if (status == ISING_ECUDA || status == ISING_ETIMEOUT) c->poisoned = status;
+    }
+    return status;
+}
+
+int cuda_fail(ising_ctx *c, cudaError_t e, const char *where)
+{
+    return fail(c, ISING_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define CK(ctx, call)                                                   \
+    do {                                                                \
+        cudaError_t e_ = (call);                                        \
+        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call);      \
+    } while (0)
+
+int check_ctx(ising_ctx *c)
+{
+    if (!c) return ISING_EINVAL;
+    if (c->poisoned) return ISING_EPOISONED;
+    return ISING_OK;
+}
+
+bool packed_L_ok(int L) { return (L >= 64 && L % 64 == 0) || L == 4 || L == 8 || L == 16 || L == 32; }
+
+// Switch to the context's device for the duration of a call.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+size_t lattice_bytes_packed(int L, int R) { return (size_t)R * 2 * (size_t)make_geom(L).nw * sizeof(uint32_t); }
+
+}  // namespace
+
+extern "C" {
+
+void ising_default_opts(ising_opts *o)
+{
+    if (!o) return;
+    o->tie = ISING_TIE_GLAUBER;
+    o->form = ISING_FORM_PACKED;
+    o->stream = nullptr;
+    o->device = -1;
+    o->variant = 0;
+    o->tile_y = 0;
+    o->tile_z = 0;
+}
+
+int64_t ising_record_len(int L)
+{
+    if (L < 4 || L % 2 != 0) return -1;
+    return 3 + 3 * (int64_t)(L / 2 + 1);
+}
+
+int64_t ising_packed_words(int L)
+{
+    if (!packed_L_ok(L)) return -1;
+    return 2 * make_geom(L).nw;
+}
+
+const char *ising_strerror(int s)
+{
+    switch (s) {
+    case ISING_OK: return "ok";
+    case ISING_EINVAL: return "invalid argument";
+    case ISING_ENOMEM: return "out of memory";
+    case ISING_ECUDA: return "CUDA error";
+    case ISING_ETIMEOUT: return "device-side wait timed out";
+    case ISING_EBUSY: return "busy";
+    case ISING_EPOISONED: return "context poisoned by an earlier error";
+    default: return "unknown status";
+    }
+}
+
+const char *ising_last_error(const ising_ctx *c) { return c ? c->err : "null context"; }
+
+int64_t ising_launch_count(const ising_ctx *c) { return c ? c->launches : -1; }
+
+int ising_variants(int *ids, int cap)
+{
+    const int all[2] = {VARIANT_WORD, VARIANT_ZMARCH};
+    if (!ids) return 2;
+    int n = 0;
+    for (int i = 0; i < 2 && n < cap; ++i) ids[n++] = all[i];
+    return n;
+}
+
+int ising_destroy(ising_ctx *c)
+{
+    if (!c) return ISING_OK;
+    {
+        DeviceGuard dg(c->device);
+        if (c->stream) cudaStreamSynchronize(c->stream);
+        cudaFree(c->lat);
+        cudaFree(c->plain);
+        cudaFree(c->rec_dev);
+        cudaFree(c->der_dev);
+        if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    }
+    delete c;
+    return ISING_OK;
+}
+
+int ising_create_ex(ising_ctx **out, int L, int R, uint64_t seed, const ising_opts *opts)
+{
+    if (!out) return ISING_EINVAL;
+    *out = nullptr;
+    ising_opts o;
+    ising_default_opts(&o);
+    if (opts) o = *opts;
+    if (L < 4 || L % 2 != 0 || R < 1 || R > 65535) return ISING_EINVAL;
+    if (o.tie < 0 || o.tie > 2 || (o.form != ISING_FORM_PACKED && o.form != ISING_FORM_PLAIN)) return ISING_EINVAL;
+    // the measurement kernels always run on the packed store
+    if (!packed_L_ok(L)) return ISING_EINVAL;
+    if ((int64_t)L > 4096) return ISING_EINVAL;  // 32-bit Philox group index bound
+    ising_ctx *c = new (std::nothrow) ising_ctx();
+    if (!c) return ISING_ENOMEM;
+    c->L = L;
+    c->R = R;
+    c->seed = seed;
+    c->opts = o;
+    c->g = make_geom(L);
+    int dev = o.device;
+    if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) {
+        delete c;
+        return ISING_ECUDA;
+    }
+    c->device = dev;
+    DeviceGuard dg(dev);
+    auto bail = [&](int s) {
+        ising_destroy(c);
+        return s;
+    };
+    if (o.stream) {
+        c->stream = (cudaStream_t)o.stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) return bail(ISING_ECUDA);
+        c->own_stream = true;
+    }
+    // sweep kernel selection
+    if (o.variant == 0) {
+        c->cfg = default_sweep_config(L, R);
+    } else {
+        c->cfg = SweepConfig{o.variant, o.tile_y, o.tile_z};
+        if (c->cfg.variant == VARIANT_ZMARCH && (o.tile_y == 0 || o.tile_z == 0)) {
+            SweepConfig d = default_sweep_config(L, R);
+            if (d.variant == VARIANT_ZMARCH) {
+                if (!o.tile_y) c->cfg.tile_y = d.tile_y;
+                if (!o.tile_z) c->cfg.tile_z = d.tile_z;
+            }
+        }
+        if (!sweep_config_valid(L, c->cfg)) return bail(ISING_EINVAL);
+    }
+    const size_t pbytes = lattice_bytes_packed(L, R);
+    if (cudaMalloc(&c->lat, pbytes) != cudaSuccess) return bail(ISING_ENOMEM);
+    if (o.form == ISING_FORM_PLAIN) {
+        const size_t nbytes = (size_t)R * (size_t)L * L * L;
+        if (cudaMalloc(&c->plain, nbytes) != cudaSuccess) return bail(ISING_ENOMEM);
+    }
+    if (cudaMalloc(&c->rec_dev, sizeof(int64_t) * (size_t)R * ising_record_len(L)) != cudaSuccess)
+        return bail(ISING_ENOMEM);
+    if (cudaMalloc(&c->der_dev, sizeof(double) * 4 * (size_t)R) != cudaSuccess) return bail(ISING_ENOMEM);
+    cudaError_t e;
+    if (o.form == ISING_FORM_PLAIN) {
+        e = launch_init_plain(c->plain, L, R, seed, c->stream);
+    } else {
+        // padded words (L < 64) must hold zeros beyond the row's L/2 bits
+        if (L < 64) {
+            e = cudaMemsetAsync(c->lat, 0, pbytes, c->stream);
+            if (e != cudaSuccess) return bail(ISING_ECUDA);
+        }
+        e = launch_init_packed(c->lat, L, R, seed, c->stream);
+    }
+    c->launches += 1;
+    if (e != cudaSuccess) return bail(ISING_ECUDA);
+    *out = c;
+    return ISING_OK;
+}
+
+int ising_create(ising_ctx **out, int L, int R, uint64_t seed) { return ising_create_ex(out, L, R, seed, nullptr); }
+
+int ising_reinit(ising_ctx *c, uint64_t seed)
+{
+    int s = check_ctx(c);
+    if (s) return s;
+    DeviceGuard dg(c->device);
+    c->seed = seed;
+    if (c->opts.form == ISING_FORM_PLAIN) {
+        CK(c, launch_init_plain(c->plain, c->L, c->R, seed, c->stream));
+    } else {
+        CK(c, launch_init_packed(c->lat, c->L, c->R, seed, c->stream));
+    }
+    c->launches += 1;
+    c->t = 0;
+    return ISING_OK;
+}
+
+int ising_sweep(ising_ctx *c, int64_t n)
+{
+    int s = check_ctx(c);
+    if (s) return s;
+    if (n < 0) return fail(c, ISING_EINVAL, "negative sweep count");
+    if (c->t + n > (int64_t)0xffffffffll) return fail(c, ISING_EINVAL, "sweep counter beyond 2^32");
+    if (n == 0) return ISING_OK;
+    DeviceGuard dg(c->device);
+    cudaError_t e;
+    if (c->opts.form == ISING_FORM_PLAIN)
+        e = launch_sweeps_plain(c->plain, c->L, c->R, c->seed, c->opts.tie, c->t, n, c->stream, &c->launches);
+    else
+        e = launch_sweeps_packed(c->lat, c->L, c->R, c->seed, c->opts.tie, c->t, n, c->cfg, c->stream, &c->launches);
+    if (e != cudaSuccess) return cuda_fail(c, e, "sweep launch");
+    c->t += n;
+    return ISING_OK;
+}
+
+int ising_measure_ex(ising_ctx *c, int64_t *rec, double *derived, double cval, unsigned flags)
+{
+    int s = check_ctx(c);
+    if (s) return s;
+    if (flags & ~(ISING_MEAS_DEVICE | ISING_MEAS_CONNECTED | ISING_MEAS_NO_CORR))
+        return fail(c, ISING_EINVAL, "unknown measure flags");
+    DeviceGuard dg(c->device);
+    const bool dev = flags & ISING_MEAS_DEVICE;
+    const bool corr = !(flags & ISING_MEAS_NO_CORR);
+    if (c->opts.form == ISING_FORM_PLAIN) {
+        CK(c, launch_pack(c->plain, c->lat, c->L, c->R, c->stream));
+        c->launches += 1;
+    }
+    int64_t *rdst = (dev && rec) ? rec : c->rec_dev;
+    CK(c, launch_measure(c->lat, c->L, c->R, c->t, corr, rdst, c->stream, &c->launches));
+    double *ddst = nullptr;
+    if (derived) {
+        ddst = dev ? derived : c->der_dev;
+        CK(c, launch_derived(rdst, c->L, c->R, cval, flags & ISING_MEAS_CONNECTED, ddst, c->stream, &c->launches));
+    }
+    if (!dev) {
+        const int64_t RL = ising_record_len(c->L);
+        if (rec) CK(c, cudaMemcpyAsync(rec, rdst, sizeof(int64_t) * RL * c->R, cudaMemcpyDeviceToHost, c->stream));
+        if (derived)
+            CK(c, cudaMemcpyAsync(derived, ddst, sizeof(double) * 4 * c->R, cudaMemcpyDeviceToHost, c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+    }
+    return ISING_OK;
+}
+
+int ising_measure(ising_ctx *c, int64_t *out)
+{
+    if (!out) return c ? fail(c, ISING_EINVAL, "null output") : ISING_EINVAL;
+    return ising_measure_ex(c, out, nullptr, 0.5, 0u);
+}
+
+int ising_get_spins(ising_ctx *c, int replica, int8_t *host_out)
+{
+    int s = check_ctx(c);
+    if (s) return s;
+    if (!host_out || replica < 0 || replica >= c->R) return fail(c, ISING_EINVAL, "bad replica or buffer");
+    DeviceGuard dg(c->device);
+    const size_t N = (size_t)c->L * c->L * c->L;
+    if (c->opts.form == ISING_FORM_PLAIN) {
+        CK(c, cudaMemcpyAsync(host_out, c->plain + (size_t)replica * N, N, cudaMemcpyDeviceToHost, c->stream));
+    } else {
+        int8_t *tmp = nullptr;
+        if (cudaMallocAsync(&tmp, N, c->stream) != cudaSuccess) return fail(c, ISING_ENOMEM, "staging buffer");
+        cudaError_t e = launch_unpack(c->lat + (size_t)replica * 2 * c->g.nw, tmp, c->L, 1, c->stream);
+        c->launches += 1;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(host_out, tmp, N, cudaMemcpyDeviceToHost, c->stream);
+        cudaFreeAsync(tmp, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "get_spins");
+    }
+    CK(c, cudaStreamSynchronize(c->stream));
+    return ISING_OK;
+}
+
+int ising_set_spins(ising_ctx *c, int replica, const int8_t *host_in)
+{
+    int s = check_ctx(c);
+    if (s) return s;
+    if (!host_in || replica < 0 || replica >= c->R) return fail(c, ISING_EINVAL, "bad replica or buffer");
+    const size_t N = (size_t)c->L * c->L * c->L;
+    for (size_t i = 0; i < N; ++i)
+        if (host_in[i] != 1 && host_in[i] != -1) return fail(c, ISING_EINVAL, "spin values must be +1 or -1");
+    DeviceGuard dg(c->device);
+    if (c->opts.form == ISING_FORM_PLAIN) {
+        CK(c, cudaMemcpyAsync(c->plain + (size_t)replica * N, host_in, N, cudaMemcpyHostToDevice, c->stream));
+    } else {
+        int8_t *tmp = nullptr;
+        if (cudaMallocAsync(&tmp, N, c->stream) != cudaSuccess) return fail(c, ISING_ENOMEM, "staging buffer");
+        cudaError_t e = cudaMemcpyAsync(tmp, host_in, N, cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = launch_pack(tmp, c->lat + (size_t)replica * 2 * c->g.nw, c->L, 1, c->stream);
+        c->launches += 1;
+        cudaFreeAsync(tmp, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "set_spins");
+    }
+    CK(c, cudaStreamSynchronize(c->stream));
+    return ISING_OK;
+}
+
+int ising_get_packed(ising_ctx *c, int replica, uint32_t *words, unsigned flags)
+{
+    int s = check_ctx(c);
+    if (s) return s;
+    if (!words || replica < 0 || replica >= c->R || (flags & ~ISING_PTR_DEVICE))
+        return fail(c, ISING_EINVAL, "bad replica, buffer or flags");
+    DeviceGuard dg(c->device);
+    if (c->opts.form == ISING_FORM_PLAIN) {
+        CK(c, launch_pack(c->plain, c->lat, c->L, c->R, c->stream));
+        c->launches += 1;
+    }
+    const size_t bytes = 2 * (size_t)c->g.nw * sizeof(uint32_t);
+    const bool dev = flags & ISING_PTR_DEVICE;
+    CK(c, cudaMemcpyAsync(words, c->lat + (size_t)replica * 2 * c->g.nw, bytes,
+                          dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    if (!dev) CK(c, cudaStreamSynchronize(c->stream));
+    return ISING_OK;
+}
+
+int ising_set_packed(ising_ctx *c, int replica, const uint32_t *words, unsigned flags)
+{
+    int s = check_ctx(c);
+    if (s) return s;
+    if (!words || replica < 0 || replica >= c->R || (flags & ~ISING_PTR_DEVICE))
+        return fail(c, ISING_EINVAL, "bad replica, buffer or flags");
+    const bool dev = flags & ISING_PTR_DEVICE;
+    if (!dev && c->L < 64) {
+        const uint32_t m = row_mask(c->g.RB);
+        for (int64_t i = 0; i < 2 * c->g.nw; ++i)
+            if (words[i] & ~m) return fail(c, ISING_EINVAL, "padding bits must be zero");
+    }
+    DeviceGuard dg(c->device);
+    const size_t bytes = 2 * (size_t)c->g.nw * sizeof(uint32_t);
+    CK(c, cudaMemcpyAsync(c->lat + (size_t)replica * 2 * c->g.nw, words, bytes,
+                          dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    if (c->opts.form == ISING_FORM_PLAIN) {
+        // expand only this replica into the byte lattice
+        const size_t N = (size_t)c->L * c->L * c->L;
+        CK(c, launch_unpack(c->lat + (size_t)replica * 2 * c->g.nw, c->plain + (size_t)replica * N, c->L, 1,
+                            c->stream));
+        c->launches += 1;
+    }
+    if (!dev) CK(c, cudaStreamSynchronize(c->stream));
+    return ISING_OK;
+}
+
+int ising_get_time(ising_ctx *c, int64_t *t)
+{
+    if (!c || !t) return ISING_EINVAL;
+    *t = c->t;
+    return ISING_OK;
+}
+
+int ising_set_time(ising_ctx *c, int64_t t)
+{
+    int s = check_ctx(c);
+    if (s) return s;
+    if (t < 0 || t > (int64_t)0xffffffffll) return fail(c, ISING_EINVAL, "time out of range");
+    c->t = t;
+    return ISING_OK;
+}
+
+int ising_sync(ising_ctx *c)
+{
+    int s = check_ctx(c);
+    if (s) return s;
+    DeviceGuard dg(c->device);
+    CK(c, cudaStreamSynchronize(c->stream));
+    return ISING_OK;
+}
+
+}  // extern "C"

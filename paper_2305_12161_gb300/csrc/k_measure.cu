@@ -1,0 +1,291 @@
+// Measurement kernels on the packed store (Eq. (2) and the energy of H = -sum s_i s_j):
+//   M = sum_i s_i, B = #unequal nearest-neighbour pairs, and the axis correlation sums
+//   D_a(r) = #{ i : s_i != s_(i + r e_a) }, a in {x,y,z}, r = 0..L/2, as int64.
+//
+// Every bond joins an even and an odd site, so B is the sum over sublattice-0 words of
+// popc(s ^ neighbour) for its six neighbour words.
+//
+// D_a(r) is computed on "columns": sequences of L words whose 32 bit lanes are 32
+// independent lines of sites along axis a.  For a line parity class pi (sites
+// x = 2k + pi) the word of row (y,z) is V_pi(y,z) = sublattice ((pi + y + z) mod 2) at
+// that row, so along y or z the words of one (kw, pi) and the other coordinate form a
+// column directly.  Along x, bundles of 32 rows are bit-transposed (warp ballots) into a
+// column T[x] whose lane b is row b of the bundle.  Then, per column,
+//   D_a(r) += sum_j popc(col[j] ^ col[(j + r) mod L]),
+// staged in shared memory (extended by L/2 words so that j + r never wraps).
+#include "common.cuh"
+#include "kernels.h"
+
+namespace ising {
+
+__device__ __forceinline__ int64_t rec_len(int L) { return 3 + 3 * (int64_t)(L / 2 + 1); }
+
+__global__ void k_rec_init(int64_t *rec, int L, int R, int64_t t, bool corr)
+{
+    const int64_t RL = rec_len(L);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < RL * R; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = i % RL;
+        rec[i] = j == 0 ? t : (j < 3 ? 0 : (corr ? 0 : -1));
+    }
+}
+
+__device__ __forceinline__ long long warp_sum(long long v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// M and B of replica blockIdx.y.
+__global__ void k_mb(const uint32_t *lat, Geom g, int64_t *rec)
+{
+    const int r = blockIdx.y;
+    const uint32_t *S0 = lat + (2 * (int64_t)r) * g.nw;
+    const uint32_t *S1 = S0 + g.nw;
+    long long m = 0, b = 0;
+    for (int64_t sw = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; sw < g.nw; sw += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t s = __ldg(S0 + sw);
+        const Nbrs n = load_nbrs(S1, g, sw, 0);
+        b += __popc(s ^ n.C) + __popc(s ^ n.X) + __popc(s ^ n.Ym) + __popc(s ^ n.Yp) + __popc(s ^ n.Zm) +
+             __popc(s ^ n.Zp);
+        m += 2 * (__popc(s) + __popc(n.C)) - 2 * g.RB;
+    }
+    __shared__ long long red[2][32];
+    m = warp_sum(m);
+    b = warp_sum(b);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        red[0][wid] = m;
+        red[1][wid] = b;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = blockDim.x >> 5;
+        m = lane < nw ? red[0][lane] : 0;
+        b = lane < nw ? red[1][lane] : 0;
+        m = warp_sum(m);
+        b = warp_sum(b);
+        if (lane == 0) {
+            const int64_t RL = rec_len(g.L);
+            atomicAdd(reinterpret_cast<unsigned long long *>(rec + r * RL + 1), (unsigned long long)m);
+            atomicAdd(reinterpret_cast<unsigned long long *>(rec + r * RL + 2), (unsigned long long)b);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// Axis correlation.  blockIdx.z = axis (0 = x, 1 = y, 2 = z), blockIdx.y = replica,
+// blockIdx.x strides over panels of NC columns.
+struct CorrShape {
+    int NC;           // columns per panel
+    int64_t ncols[3]; // columns per replica for each axis
+};
+
+__host__ __device__ inline int corr_nc(int L)
+{
+    int nc = 8192 / L;
+    if (nc < 1) nc = 1;
+    if (nc > 64) nc = 64;
+    return nc;
+}
+
+__host__ __device__ inline int64_t corr_ncols(const Geom &g, int axis)
+{
+    if (axis == 0) return ((int64_t)g.L * g.L + 31) / 32;  // 32-row bundles
+    return 2 * (int64_t)g.L * g.W;                          // (pi, other coordinate, kw)
+}
+
+// Stage columns c0 .. c0+NC-1 of the y or z axis into sm[c*LE + j], j < L + L/2
+// (column (pi, a, kw): a is z for the y axis, y for the z axis; element j is the other
+// coordinate, wrapped).  Consecutive threads take consecutive columns of one j, which
+// are consecutive words in memory.
+__device__ __forceinline__ void load_panel_yz(const uint32_t *S0, const uint32_t *S1, const Geom &g, int axis,
+                                              int64_t c0, int NC, int64_t ncols, uint32_t *sm, int LE,
+                                              int tid0, int stride)
+{
+    const int L = g.L, W = g.W;
+    for (int e = tid0; e < NC * LE; e += stride) {
+        const int j = e / NC;
+        const int c = e - j * NC;
+        const int64_t col = c0 + c;
+        uint32_t v = 0u;
+        if (col < ncols) {
+            const int pi = (int)(col / ((int64_t)L * W));
+            const int64_t rem = col - (int64_t)pi * L * W;
+            const int a = (int)(rem / W);
+            const int kw = (int)(rem - (int64_t)a * W);
+            const int jj = j < L ? j : j - L;
+            const int y = axis == 1 ? jj : a;
+            const int z = axis == 1 ? a : jj;
+            const uint32_t *Sq = ((pi + y + z) & 1) ? S1 : S0;
+            v = __ldg(Sq + ((int64_t)z * L + y) * W + kw);
+        }
+        sm[c * LE + j] = v;
+    }
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT) k_corr(const uint32_t *lat, Geom g, int64_t *rec)
+{
+    extern __shared__ uint32_t csm[];
+    const int axis = blockIdx.z;
+    const int r = blockIdx.y;
+    const int L = g.L, H = L / 2, LE = L + L / 2;
+    const int NC = corr_nc(L);
+    const uint32_t *S0 = lat + (2 * (int64_t)r) * g.nw;
+    const uint32_t *S1 = S0 + g.nw;
+    uint32_t *cols = csm;                                           // NC * LE words
+    unsigned long long *acc = reinterpret_cast<unsigned long long *>(csm + ((NC * LE + 1) & ~1));  // H+1
+    const int tid = threadIdx.x;
+    for (int i = tid; i <= H; i += NT) acc[i] = 0ull;
+    const int64_t ncols = corr_ncols(g, axis);
+    const int64_t npanels = (ncols + NC - 1) / NC;
+    const int lane = tid & 31, wid = tid >> 5;
+    for (int64_t pnl = blockIdx.x; pnl < npanels; pnl += gridDim.x) {
+        __syncthreads();  // previous panel fully consumed
+        const int64_t c0 = pnl * NC;
+        const int nc = (int)min((int64_t)NC, ncols - c0);
+        if (axis != 0) {
+            load_panel_yz(S0, S1, g, axis, c0, NC, ncols, cols, LE, tid, NT);
+        } else {
+            // bundle b = rows 32b .. 32b+31 (row = y + L z); T[x] lane i = site (x, row 32b+i).
+            // Tasks: (bundle, pi, kw), one warp each, 32 ballots per task.
+            const int ntask = NC * 2 * g.W;
+            for (int task = wid; task < ntask; task += NT / 32) {
+                const int c = task / (2 * g.W);
+                const int rem = task - c * 2 * g.W;
+                const int pi = rem / g.W, kw = rem - pi * g.W;
+                const int64_t row = (c0 + c) * 32 + lane;
+                uint32_t v = 0u;
+                if (c < nc && row < (int64_t)L * L) {
+                    const int y = (int)(row % L), z = (int)(row / L);
+                    const uint32_t *Sq = ((pi + y + z) & 1) ? S1 : S0;
+                    v = __ldg(Sq + row * g.W + kw);
+                }
+                uint32_t mine = 0u;
+                for (int k = 0; k < g.RB; ++k) {
+                    const unsigned bal = __ballot_sync(0xffffffffu, (v >> k) & 1u);
+                    if (lane == k) mine = bal;
+                }
+                if (lane < g.RB) {
+                    const int x = 2 * (32 * kw + lane) + pi;
+                    cols[c * LE + x] = mine;
+                    if (x < H) cols[c * LE + L + x] = mine;
+                }
+            }
+        }
+        __syncthreads();
+        // pairs (column c, lag rr = 1..H): consecutive threads take consecutive lags.
+        const int npairs = NC * H;
+        for (int e = tid; e < npairs; e += NT) {
+            const int c = e / H;
+            const int rr = 1 + (e - c * H);
+            const uint32_t *col = cols + c * LE;
+            unsigned int s = 0;
+            int j = 0;
+            for (; j + 4 <= L; j += 4) {
+                s += __popc(col[j] ^ col[j + rr]) + __popc(col[j + 1] ^ col[j + 1 + rr]) +
+                     __popc(col[j + 2] ^ col[j + 2 + rr]) + __popc(col[j + 3] ^ col[j + 3 + rr]);
+            }
+            for (; j < L; ++j) s += __popc(col[j] ^ col[j + rr]);
+            atomicAdd(acc + rr, (unsigned long long)s);
+        }
+    }
+    __syncthreads();
+    int64_t *D = rec + r * rec_len(L) + 3 + (int64_t)axis * (H + 1);
+    for (int i = 1 + tid; i <= H; i += NT)
+        if (acc[i]) atomicAdd(reinterpret_cast<unsigned long long *>(D + i), acc[i]);
+}
+
+static size_t corr_smem(int L)
+{
+    const int NC = corr_nc(L);
+    const size_t words = ((size_t)NC * (L + L / 2) + 1) & ~(size_t)1;
+    return words * 4 + (size_t)(L / 2 + 1) * 8;
+}
+
+cudaError_t launch_measure(const uint32_t *lat, int L, int R, int64_t t, bool corr, int64_t *rec, cudaStream_t s,
+                           int64_t *launches)
+{
+    const Geom g = make_geom(L);
+    const int64_t RL = 3 + 3 * (int64_t)(L / 2 + 1);
+    int64_t nb = (RL * R + 255) / 256;
+    if (nb > 4096) nb = 4096;
+    k_rec_init<<<(unsigned)nb, 256, 0, s>>>(rec, L, R, t, corr);
+    int64_t mb = (g.nw + 255) / 256;
+    if (mb > 152 * 8) mb = 152 * 8;
+    k_mb<<<dim3((unsigned)mb, (unsigned)R), 256, 0, s>>>(lat, g, rec);
+    int n = 2;
+    if (corr) {
+        const size_t smem = corr_smem(L);
+        cudaError_t e = cudaFuncSetAttribute(k_corr<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (e != cudaSuccess) return e;
+        int dev = 0, sms = 0, occ = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_corr<256>, 256, smem)) != cudaSuccess) return e;
+        if (occ < 1) occ = 1;
+        int64_t maxc = corr_ncols(g, 0);
+        if (corr_ncols(g, 1) > maxc) maxc = corr_ncols(g, 1);
+        const int NC = corr_nc(L);
+        int64_t panels = (maxc + NC - 1) / NC;
+        // persistent: one resident wave over the 3 axes and R replicas
+        int64_t want = ((int64_t)occ * sms) / ((int64_t)3 * R);
+        if (want < 1) want = 1;
+        if (panels > want) panels = want;
+        k_corr<256><<<dim3((unsigned)panels, (unsigned)R, 3), 256, smem, s>>>(lat, g, rec);
+        ++n;
+    }
+    if (launches) *launches += n;
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------
+// Derived quantities (double precision): e = -3 + 2B/N, m = M/N, l_E = N/B, and the
+// first linear-interpolated crossing l_C of C(r) = sum_a (N - 2 D_a(r)) / (3N) (- m^2
+// when connected) with the constant c (Results: c = 0.5).
+__global__ void k_derived(const int64_t *rec, int L, int R, double c, bool connected, double *out)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    const int64_t H = L / 2;
+    const int64_t *q = rec + (int64_t)r * (3 + 3 * (H + 1));
+    const double N = (double)L * (double)L * (double)L;
+    const int64_t M = q[1], B = q[2];
+    const int64_t *Dx = q + 3, *Dy = q + 3 + (H + 1), *Dz = q + 3 + 2 * (H + 1);
+    const double m = __ddiv_rn((double)M, N);
+    double *o = out + 4 * (int64_t)r;
+    o[0] = __dadd_rn(-3.0, __ddiv_rn(__dmul_rn(2.0, (double)B), N));
+    o[1] = m;
+    o[2] = B == 0 ? __longlong_as_double(0x7ff0000000000000ll) : __ddiv_rn(N, (double)B);
+    double lc = __longlong_as_double(0x7ff8000000000000ll);
+    const double sub = connected ? __dmul_rn(m, m) : 0.0;
+    const double N3 = __dmul_rn(3.0, N);
+    if (Dx[0] >= 0) {
+        for (int64_t k = 0; k < H; ++k) {
+            const double g0 = __dadd_rn(__dadd_rn(__dsub_rn(N, __dmul_rn(2.0, (double)Dx[k])),
+                                                  __dsub_rn(N, __dmul_rn(2.0, (double)Dy[k]))),
+                                        __dsub_rn(N, __dmul_rn(2.0, (double)Dz[k])));
+            const double g1 = __dadd_rn(__dadd_rn(__dsub_rn(N, __dmul_rn(2.0, (double)Dx[k + 1])),
+                                                  __dsub_rn(N, __dmul_rn(2.0, (double)Dy[k + 1]))),
+                                        __dsub_rn(N, __dmul_rn(2.0, (double)Dz[k + 1])));
+            const double c0 = __dsub_rn(__ddiv_rn(g0, N3), sub);
+            const double c1 = __dsub_rn(__ddiv_rn(g1, N3), sub);
+            if (c0 >= c && c > c1) {
+                lc = __dadd_rn((double)k, __ddiv_rn(__dsub_rn(c0, c), __dsub_rn(c0, c1)));
+                break;
+            }
+        }
+    }
+    o[3] = lc;
+}
+
+cudaError_t launch_derived(const int64_t *rec, int L, int R, double c, bool connected, double *derived,
+                           cudaStream_t s, int64_t *launches)
+{
+    k_derived<<<(R + 127) / 128, 128, 0, s>>>(rec, L, R, c, connected, derived);
+    if (launches) *launches += 1;
+    return cudaGetLastError();
+}
+
+}  // namespace ising

@@ -1,0 +1,288 @@
+// Packed-form kernels: the T = infinity initial state and the checkerboard half-sweep
+// (Methods, "Checkerboard update"; acceptance Eq. (6) at T -> 0) on 1-bit sublattices.
+//
+// Two sweep variants, bit-identical:
+//   WORD   — one thread per 32-bit word; neighbours through the read-only cache.  Any
+//            supported L (multiples of 64, and 4..32 with one padded word per row).
+//   ZMARCH — for L >= 256 (a row is W/4 >= 1 uint4): a CTA owns a tile of TY full
+//            rows and marches it through TZ consecutive planes.  Planes of the other
+//            sublattice (with one halo row above and below) and of the own sublattice
+//            stream into a shared-memory ring through cp.async, two planes ahead, so
+//            every word of either array is read from HBM about once per half-sweep.
+//            Each thread updates 128 spins (one uint4, one Philox group) per plane.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace ising {
+
+// ---------------------------------------------------------------------------------
+// Initial state: sublattice q of replica r is the Philox output of phase 2+q at t = 0.
+__global__ void k_init_packed_wide(uint32_t *lat, Geom g, uint64_t seed)
+{
+    // L >= 64: storage words coincide with compressed-index words; one Philox call
+    // yields the four words of a group.
+    const int r = blockIdx.y, q = blockIdx.z;
+    uint4 *S4 = reinterpret_cast<uint4 *>(lat + (2 * (int64_t)r + q) * g.nw);
+    const uint64_t S = seed + (uint64_t)r;
+    const int64_t ng = g.nw >> 2;
+    for (int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gi < ng;
+         gi += (int64_t)gridDim.x * blockDim.x) {
+        const U4 o = philox4x32_10((uint32_t)gi, 0u, (uint32_t)(2 + q), 0u, (uint32_t)S, (uint32_t)(S >> 32));
+        S4[gi] = make_uint4(o.x, o.y, o.z, o.w);
+    }
+}
+
+__global__ void k_init_packed_small(uint32_t *lat, Geom g, uint64_t seed)
+{
+    const int r = blockIdx.y, q = blockIdx.z;
+    uint32_t *Sq = lat + (2 * (int64_t)r + q) * g.nw;
+    const uint64_t S = seed + (uint64_t)r;
+    for (int64_t sw = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; sw < g.nw;
+         sw += (int64_t)gridDim.x * blockDim.x)
+        Sq[sw] = rng_word(g, sw, 0u, (uint32_t)(2 + q), S);
+}
+
+static int grid_for(int64_t items, int block, int cap)
+{
+    int64_t b = (items + block - 1) / block;
+    if (b < 1) b = 1;
+    if (b > cap) b = cap;
+    return (int)b;
+}
+
+cudaError_t launch_init_packed(uint32_t *lat, int L, int R, uint64_t seed, cudaStream_t s)
+{
+    const Geom g = make_geom(L);
+    if (L >= 64) {
+        dim3 grid(grid_for(g.nw / 4, 256, 65535), R, 2);
+        k_init_packed_wide<<<grid, 256, 0, s>>>(lat, g, seed);
+    } else {
+        dim3 grid(grid_for(g.nw, 256, 65535), R, 2);
+        k_init_packed_small<<<grid, 256, 0, s>>>(lat, g, seed);
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------
+// WORD variant: one 32-bit word (32 spins of one row) per thread.
+template <int RULE>
+__global__ void k_sweep_word(uint32_t *lat, Geom g, int q, uint32_t t, uint64_t seed)
+{
+    const int r = blockIdx.y;
+    uint32_t *S = lat + (2 * (int64_t)r + q) * g.nw;
+    const uint32_t *O = lat + (2 * (int64_t)r + (1 - q)) * g.nw;
+    const uint64_t key = seed + (uint64_t)r;
+    for (int64_t sw = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; sw < g.nw;
+         sw += (int64_t)gridDim.x * blockDim.x) {
+        const Nbrs n = load_nbrs(O, g, sw, q);
+        uint32_t ge4, eq3;
+        count6(n.C, n.X, n.Ym, n.Yp, n.Zm, n.Zp, ge4, eq3);
+        const uint32_t s = S[sw];
+        uint32_t rnd = 0u;
+        if (RULE == TIE_GLAUBER && eq3 != 0u) rnd = rng_word(g, sw, t, (uint32_t)q, key);
+        S[sw] = resolve<RULE>(s, ge4, eq3, rnd);
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// ZMARCH variant.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+constexpr int ZM_AHEAD = 2;            // copy groups in flight beyond the one consumed
+constexpr int ZM_NSO = 3 + ZM_AHEAD;   // ring slots for other-sublattice planes
+constexpr int ZM_NSQ = 1 + ZM_AHEAD;   // ring slots for own-sublattice planes
+
+static size_t zmarch_smem_bytes(int L, int TY)
+{
+    const int W4 = L / 256;
+    return sizeof(uint4) * (size_t)(ZM_NSO * (TY + 2) * W4 + ZM_NSQ * TY * W4);
+}
+
+// Copy group gi (gi = 0, 1, ...) of a tile holds the other sublattice's plane
+// z0 - 1 + gi (TY + 2 rows: the tile and one halo row on each side) and, for gi >= 2,
+// the own sublattice's plane z0 + gi - 2.  Step i (plane z = z0 + i) needs the other
+// planes z-1, z, z+1 (groups i, i+1, i+2) and own plane z (group i+2).
+template <int RULE>
+__global__ void __launch_bounds__(1024) k_sweep_zmarch(uint32_t *lat, Geom g, int q, uint32_t t,
+                                                       uint64_t seed, int TY, int TZ)
+{
+    extern __shared__ uint4 zsm[];
+    const int L = g.L;
+    const int W4 = g.W >> 2;
+    const int NT = blockDim.x;  // TY * W4
+    const int tid = threadIdx.x;
+    const int ty = tid / W4, cx = tid - ty * W4;
+    const int nty = L / TY;
+    const int y0 = (int)(blockIdx.x % nty) * TY;
+    const int z0 = (int)(blockIdx.x / nty) * TZ;
+    const int r = blockIdx.y;
+    uint4 *S4 = reinterpret_cast<uint4 *>(lat + (2 * (int64_t)r + q) * g.nw);
+    const uint4 *O4 = reinterpret_cast<const uint4 *>(lat + (2 * (int64_t)r + (1 - q)) * g.nw);
+    const uint64_t key = seed + (uint64_t)r;
+    const int OSZ = (TY + 2) * W4;
+    const int QSZ = TY * W4;
+    uint4 *osm = zsm;
+    uint4 *qsm = zsm + ZM_NSO * OSZ;
+    const int64_t plane4 = (int64_t)L * W4;
+
+    auto issue = [&](int gi) {
+        if (gi <= TZ + 1) {
+            int pz = z0 - 1 + gi;
+            pz = pz < 0 ? pz + L : (pz >= L ? pz - L : pz);
+            uint4 *dst = osm + (gi % ZM_NSO) * OSZ;
+            const uint4 *src = O4 + (int64_t)pz * plane4;
+            for (int e = tid; e < OSZ; e += NT) {
+                const int ry = e / W4, ex = e - ry * W4;
+                int yy = y0 - 1 + ry;
+                yy = yy < 0 ? yy + L : (yy >= L ? yy - L : yy);
+                cp_async16(dst + e, src + (int64_t)yy * W4 + ex);
+            }
+        }
+        if (gi >= 2 && gi <= TZ + 1) {
+            const int pz = z0 + gi - 2;
+            cp_async16(qsm + (gi % ZM_NSQ) * QSZ + tid, S4 + (int64_t)pz * plane4 + (int64_t)(y0 + ty) * W4 + cx);
+        }
+        cp_async_commit();
+    };
+
+#pragma unroll 1
+    for (int gi = 0; gi < ZM_AHEAD + 2; ++gi) issue(gi);
+
+    const int y = y0 + ty;
+    const int cxl = cx == 0 ? W4 - 1 : cx - 1;
+    const int cxr = cx == W4 - 1 ? 0 : cx + 1;
+#pragma unroll 1
+    for (int i = 0; i < TZ; ++i) {
+        cp_async_wait<ZM_AHEAD - 1>();
+        __syncthreads();
+        issue(i + 2 + ZM_AHEAD);  // refills the slots read in step i-1 only
+
+        const int z = z0 + i;
+        const uint4 *Oz = osm + ((i + 1) % ZM_NSO) * OSZ;
+        const uint4 c = Oz[(ty + 1) * W4 + cx];
+        const uint4 ym = Oz[ty * W4 + cx];
+        const uint4 yp = Oz[(ty + 2) * W4 + cx];
+        const uint4 zm = osm[(i % ZM_NSO) * OSZ + (ty + 1) * W4 + cx];
+        const uint4 zp = osm[((i + 2) % ZM_NSO) * OSZ + (ty + 1) * W4 + cx];
+        const uint4 s = qsm[((i + 2) % ZM_NSQ) * QSZ + tid];
+        const int p = (y + z + q) & 1;
+        uint4 X;
+        if (p == 0) {  // x-1 neighbour: bit k-1, carried in from the word on the left
+            const uint32_t e = Oz[(ty + 1) * W4 + cxl].w;
+            X.x = __funnelshift_l(e, c.x, 1);
+            X.y = __funnelshift_l(c.x, c.y, 1);
+            X.z = __funnelshift_l(c.y, c.z, 1);
+            X.w = __funnelshift_l(c.z, c.w, 1);
+        } else {       // x+1 neighbour: bit k+1, carried in from the word on the right
+            const uint32_t e = Oz[(ty + 1) * W4 + cxr].x;
+            X.x = __funnelshift_r(c.x, c.y, 1);
+            X.y = __funnelshift_r(c.y, c.z, 1);
+            X.z = __funnelshift_r(c.z, c.w, 1);
+            X.w = __funnelshift_r(c.w, e, 1);
+        }
+        uint32_t g0, g1, g2, g3, e0, e1, e2, e3;
+        count6(c.x, X.x, ym.x, yp.x, zm.x, zp.x, g0, e0);
+        count6(c.y, X.y, ym.y, yp.y, zm.y, zp.y, g1, e1);
+        count6(c.z, X.z, ym.z, yp.z, zm.z, zp.z, g2, e2);
+        count6(c.w, X.w, ym.w, yp.w, zm.w, zp.w, g3, e3);
+        const int64_t gidx = ((int64_t)z * L + y) * W4 + cx;  // Philox group = word >> 2
+        U4 o{0u, 0u, 0u, 0u};
+        if (RULE == TIE_GLAUBER && (e0 | e1 | e2 | e3) != 0u)
+            o = philox4x32_10((uint32_t)gidx, t, (uint32_t)q, 0u, (uint32_t)key, (uint32_t)(key >> 32));
+        uint4 nw;
+        nw.x = resolve<RULE>(s.x, g0, e0, o.x);
+        nw.y = resolve<RULE>(s.y, g1, e1, o.y);
+        nw.z = resolve<RULE>(s.z, g2, e2, o.z);
+        nw.w = resolve<RULE>(s.w, g3, e3, o.w);
+        S4[gidx] = nw;
+    }
+    cp_async_wait<0>();
+}
+
+// ---------------------------------------------------------------------------------
+bool sweep_config_valid(int L, const SweepConfig &c)
+{
+    if (c.variant == VARIANT_WORD) return true;
+    if (c.variant != VARIANT_ZMARCH) return false;
+    if (L < 256 || L % 256 != 0) return false;
+    const int W4 = L / 256;
+    if (c.tile_y < 1 || c.tile_z < 1 || L % c.tile_y != 0 || L % c.tile_z != 0) return false;
+    if (c.tile_y * W4 > 1024 || c.tile_y * W4 < 32) return false;
+    if (zmarch_smem_bytes(L, c.tile_y) > 200 * 1024) return false;
+    return true;
+}
+
+SweepConfig default_sweep_config(int L, int R)
+{
+    SweepConfig c{VARIANT_WORD, 0, 0};
+    if (L >= 256 && L % 256 == 0) {
+        const int W4 = L / 256;
+        int ty = 256 / W4;
+        if (ty < 8) ty = 8;
+        while (ty > 1 && (L % ty != 0 || ty * W4 > 1024)) ty >>= 1;
+        int tz = 32;
+        while (tz > 1 && L % tz != 0) tz >>= 1;
+        // keep at least ~4 CTAs per SM-worth of tiles on small lattices
+        while (tz > 4 && (int64_t)(L / ty) * (L / tz) * R < 4 * 152) tz >>= 1;
+        c = SweepConfig{VARIANT_ZMARCH, ty, tz};
+        if (!sweep_config_valid(L, c)) c = SweepConfig{VARIANT_WORD, 0, 0};
+    }
+    return c;
+}
+
+template <int RULE>
+static cudaError_t sweeps_rule(uint32_t *lat, int L, int R, uint64_t seed, int64_t t0, int64_t n,
+                               const SweepConfig &cfg, cudaStream_t s, int64_t *launches)
+{
+    const Geom g = make_geom(L);
+    if (cfg.variant == VARIANT_ZMARCH) {
+        const int W4 = L / 256;
+        const size_t smem = zmarch_smem_bytes(L, cfg.tile_y);
+        static bool attr_set = false;  // idempotent; benign if repeated
+        if (!attr_set) {
+            cudaError_t e = cudaFuncSetAttribute(k_sweep_zmarch<RULE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 200 * 1024);
+            if (e != cudaSuccess) return e;
+            attr_set = true;
+        }
+        const dim3 grid((unsigned)((L / cfg.tile_y) * (L / cfg.tile_z)), (unsigned)R);
+        const int block = cfg.tile_y * W4;
+        for (int64_t k = 0; k < n; ++k) {
+            const uint32_t t = (uint32_t)(t0 + k);
+            k_sweep_zmarch<RULE><<<grid, block, smem, s>>>(lat, g, 0, t, seed, cfg.tile_y, cfg.tile_z);
+            k_sweep_zmarch<RULE><<<grid, block, smem, s>>>(lat, g, 1, t, seed, cfg.tile_y, cfg.tile_z);
+        }
+    } else {
+        const dim3 grid((unsigned)grid_for(g.nw, 256, 8 * 152 * 4), (unsigned)R);
+        for (int64_t k = 0; k < n; ++k) {
+            const uint32_t t = (uint32_t)(t0 + k);
+            k_sweep_word<RULE><<<grid, 256, 0, s>>>(lat, g, 0, t, seed);
+            k_sweep_word<RULE><<<grid, 256, 0, s>>>(lat, g, 1, t, seed);
+        }
+    }
+    if (launches) *launches += 2 * n;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sweeps_packed(uint32_t *lat, int L, int R, uint64_t seed, int rule, int64_t t0, int64_t n,
+                                 const SweepConfig &cfg, cudaStream_t s, int64_t *launches)
+{
+    if (n <= 0) return cudaSuccess;
+    switch (rule) {
+    case TIE_GLAUBER: return sweeps_rule<TIE_GLAUBER>(lat, L, R, seed, t0, n, cfg, s, launches);
+    case TIE_ALWAYS: return sweeps_rule<TIE_ALWAYS>(lat, L, R, seed, t0, n, cfg, s, launches);
+    default: return sweeps_rule<TIE_NEVER>(lat, L, R, seed, t0, n, cfg, s, launches);
+    }
+}
+
+}  // namespace ising

@@ -1,0 +1,53 @@
+// Host-side launch wrappers of the library's kernels.  Every wrapper enqueues on
+// `stream` and returns cudaGetLastError() of its launch(es).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ising {
+
+// ---- packed form: lat points at replica 0; replica r's sublattice q starts at
+//      lat + (2*r + q) * nw. -------------------------------------------------------
+cudaError_t launch_init_packed(uint32_t *lat, int L, int R, uint64_t seed, cudaStream_t s);
+
+// Packed sweep variants (bit-identical results).
+enum SweepVariant : int {
+    VARIANT_AUTO = 0,
+    VARIANT_WORD = 1,    // one thread per 32-bit word, any supported L
+    VARIANT_ZMARCH = 2,  // z-marching, cp.async-staged tiles, 128 spins per thread, L >= 256
+};
+
+struct SweepConfig {
+    int variant;
+    int tile_y;  // rows per tile (z-march)
+    int tile_z;  // planes per tile (z-march)
+};
+
+bool sweep_config_valid(int L, const SweepConfig &c);
+SweepConfig default_sweep_config(int L, int R);
+
+// n_mcs sweeps from completed-sweep count t0; returns the number of launches through
+// *launches.
+cudaError_t launch_sweeps_packed(uint32_t *lat, int L, int R, uint64_t seed, int rule, int64_t t0,
+                                 int64_t n_mcs, const SweepConfig &cfg, cudaStream_t s,
+                                 int64_t *launches);
+
+// ---- plain form: one byte per spin, replica r at plain + r*N. --------------------
+cudaError_t launch_init_plain(int8_t *plain, int L, int R, uint64_t seed, cudaStream_t s);
+cudaError_t launch_sweeps_plain(int8_t *plain, int L, int R, uint64_t seed, int rule, int64_t t0,
+                                int64_t n_mcs, cudaStream_t s, int64_t *launches);
+// plain -> packed (for the shared measurement kernels) and back.
+cudaError_t launch_pack(const int8_t *plain, uint32_t *lat, int L, int R, cudaStream_t s);
+cudaError_t launch_unpack(const uint32_t *lat, int8_t *plain, int L, int R, cudaStream_t s);
+
+// ---- measurement on the packed store ----------------------------------------------
+// rec: R records of 3 + 3*(L/2+1) int64 (must not alias lat).  Writes t, M, B and,
+// if corr, D_a(r); otherwise D_a(r) = -1.
+cudaError_t launch_measure(const uint32_t *lat, int L, int R, int64_t t, bool corr, int64_t *rec,
+                           cudaStream_t s, int64_t *launches);
+// derived: R x [e, m, l_E, l_C]
+cudaError_t launch_derived(const int64_t *rec, int L, int R, double c, bool connected, double *derived,
+                           cudaStream_t s, int64_t *launches);
+
+}  // namespace ising

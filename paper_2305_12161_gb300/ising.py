@@ -1,0 +1,269 @@
+"""Python binding of the C ABI in ``include/ising.h`` (argument marshalling only).
+
+Every function below forwards to the entry point of the same name in ``libising.so``;
+all computation runs in the library's CUDA kernels.  There is no CPU fallback: if the
+library cannot be loaded, :func:`lib` raises.
+
+Buffers are numpy arrays (host memory) or, for the ``*_device`` forms, any object with
+a ``data_ptr()`` method (a CUDA ``torch.Tensor``) or an integer device address.
+Streams are ``torch.cuda.Stream`` objects, raw ``cudaStream_t`` integers, or None.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libising.so")
+_lock = threading.Lock()
+_lib = None
+
+ISING_OK, ISING_EINVAL, ISING_ENOMEM, ISING_ECUDA, ISING_ETIMEOUT, ISING_EBUSY, ISING_EPOISONED = 0, -1, -2, -3, -4, -5, -6
+TIE_GLAUBER, TIE_ALWAYS, TIE_NEVER = 0, 1, 2
+FORM_PACKED, FORM_PLAIN = 0, 1
+MEAS_DEVICE, MEAS_CONNECTED, MEAS_NO_CORR = 1, 2, 4
+PTR_DEVICE = 1
+VARIANT_AUTO, VARIANT_WORD, VARIANT_ZMARCH = 0, 1, 2
+
+
+class IsingError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        msg = f"{where}: {ising_strerror(status)} ({status})"
+        if detail:
+            msg += f": {detail}"
+        super().__init__(msg)
+
+
+class ising_opts(ctypes.Structure):
+    _fields_ = [("tie", ctypes.c_int), ("form", ctypes.c_int), ("stream", ctypes.c_void_p),
+                ("device", ctypes.c_int), ("variant", ctypes.c_int), ("tile_y", ctypes.c_int),
+                ("tile_z", ctypes.c_int)]
+
+
+def lib_path() -> str:
+    return _LIB_PATH
+
+
+def lib() -> ctypes.CDLL:
+    """Load ``libising.so`` (built by ``__graft_entry__.build()``); raise if absent."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_LIB_PATH):
+                raise RuntimeError(f"CUDA library {_LIB_PATH} is missing: run __graft_entry__.build() first")
+            L = ctypes.CDLL(_LIB_PATH)
+            vp, i64p = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)
+            sig = {
+                "ising_default_opts": (None, [ctypes.POINTER(ising_opts)]),
+                "ising_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int, ctypes.c_uint64]),
+                "ising_create_ex": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
+                                                   ctypes.POINTER(ising_opts)]),
+                "ising_sweep": (ctypes.c_int, [vp, ctypes.c_int64]),
+                "ising_reinit": (ctypes.c_int, [vp, ctypes.c_uint64]),
+                "ising_record_len": (ctypes.c_int64, [ctypes.c_int]),
+                "ising_measure": (ctypes.c_int, [vp, vp]),
+                "ising_measure_ex": (ctypes.c_int, [vp, vp, vp, ctypes.c_double, ctypes.c_uint]),
+                "ising_get_spins": (ctypes.c_int, [vp, ctypes.c_int, vp]),
+                "ising_set_spins": (ctypes.c_int, [vp, ctypes.c_int, vp]),
+                "ising_packed_words": (ctypes.c_int64, [ctypes.c_int]),
+                "ising_get_packed": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_uint]),
+                "ising_set_packed": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_uint]),
+                "ising_get_time": (ctypes.c_int, [vp, i64p]),
+                "ising_set_time": (ctypes.c_int, [vp, ctypes.c_int64]),
+                "ising_sync": (ctypes.c_int, [vp]),
+                "ising_destroy": (ctypes.c_int, [vp]),
+                "ising_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+                "ising_last_error": (ctypes.c_char_p, [vp]),
+                "ising_launch_count": (ctypes.c_int64, [vp]),
+                "ising_variants": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
+            }
+            for name, (res, args) in sig.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)  # torch.cuda.Stream
+
+
+def _dev_ptr(buf) -> int:
+    if isinstance(buf, int):
+        return buf
+    return int(buf.data_ptr())
+
+
+def _host(a: np.ndarray, dtype, n: int, name: str) -> np.ndarray:
+    if not isinstance(a, np.ndarray) or a.dtype != dtype or not a.flags.c_contiguous or a.size < n:
+        raise ValueError(f"{name} must be a C-contiguous numpy {np.dtype(dtype).name} array of >= {n} values")
+    return a
+
+
+def ising_strerror(status: int) -> str:
+    try:
+        return lib().ising_strerror(status).decode()
+    except Exception:  # library not loadable: still report the code
+        return f"status {status}"
+
+
+def ising_record_len(L: int) -> int:
+    return int(lib().ising_record_len(L))
+
+
+def ising_packed_words(L: int) -> int:
+    return int(lib().ising_packed_words(L))
+
+
+def ising_variants() -> list[int]:
+    buf = (ctypes.c_int * 16)()
+    n = lib().ising_variants(buf, 16)
+    return list(buf[:n])
+
+
+class Ising:
+    """One context: ``replicas`` lattices of size ``L`` (replica r seeded ``seed + r``)."""
+
+    def __init__(self, L: int, replicas: int = 1, seed: int = 1, tie: int = TIE_GLAUBER, form: int = FORM_PACKED,
+                 stream=None, device: int = -1, variant: int = 0, tile_y: int = 0, tile_z: int = 0):
+        self._h = ctypes.c_void_p()
+        o = ising_opts()
+        lib().ising_default_opts(ctypes.byref(o))
+        o.tie, o.form, o.device, o.variant, o.tile_y, o.tile_z = tie, form, device, variant, tile_y, tile_z
+        sh = _stream_handle(stream)
+        o.stream = sh if sh else None
+        self._stream_obj = stream  # keep the caller's stream alive
+        st = lib().ising_create_ex(ctypes.byref(self._h), L, replicas, seed % 2**64, ctypes.byref(o))
+        if st != ISING_OK:
+            raise IsingError(st, "ising_create_ex")
+        self.L, self.replicas, self.seed = L, replicas, seed
+        self.record_len = ising_record_len(L)
+        self.N = L**3
+
+    # -- helpers -----------------------------------------------------------------
+    def _check(self, st: int, where: str) -> None:
+        if st != ISING_OK:
+            detail = lib().ising_last_error(self._h) if self._h else b""
+            raise IsingError(st, where, (detail or b"").decode())
+
+    @property
+    def handle(self) -> int:
+        return int(self._h.value or 0)
+
+    # -- entry points ------------------------------------------------------------
+    def reinit(self, seed: int) -> None:
+        """Redraw the T = infinity start (replica r: seed + r) and reset t to 0."""
+        self._check(lib().ising_reinit(self._h, seed % 2**64), "ising_reinit")
+        self.seed = seed
+
+    def sweep(self, n_mcs: int) -> None:
+        self._check(lib().ising_sweep(self._h, n_mcs), "ising_sweep")
+
+    def measure(self, out: np.ndarray | None = None) -> np.ndarray:
+        """Records [replicas, record_len] int64 in host memory (synchronises)."""
+        if out is None:
+            out = np.empty((self.replicas, self.record_len), dtype=np.int64)
+        _host(out, np.int64, self.replicas * self.record_len, "out")
+        self._check(lib().ising_measure(self._h, out.ctypes.data), "ising_measure")
+        return out
+
+    def measure_ex(self, c: float = 0.5, connected: bool = False, corr: bool = True):
+        """(records [R, record_len] int64, derived [R, 4] float64) in host memory."""
+        rec = np.empty((self.replicas, self.record_len), dtype=np.int64)
+        der = np.empty((self.replicas, 4), dtype=np.float64)
+        flags = (MEAS_CONNECTED if connected else 0) | (0 if corr else MEAS_NO_CORR)
+        self._check(lib().ising_measure_ex(self._h, rec.ctypes.data, der.ctypes.data, c, flags), "ising_measure_ex")
+        return rec, der
+
+    def measure_device(self, rec, derived=None, c: float = 0.5, connected: bool = False, corr: bool = True) -> None:
+        """Enqueue a measurement into device buffers (no synchronisation)."""
+        flags = MEAS_DEVICE | (MEAS_CONNECTED if connected else 0) | (0 if corr else MEAS_NO_CORR)
+        dp = _dev_ptr(derived) if derived is not None else None
+        self._check(lib().ising_measure_ex(self._h, _dev_ptr(rec), dp, c, flags), "ising_measure_ex")
+
+    def get_spins(self, replica: int = 0) -> np.ndarray:
+        out = np.empty((self.L, self.L, self.L), dtype=np.int8)
+        self._check(lib().ising_get_spins(self._h, replica, out.ctypes.data), "ising_get_spins")
+        return out
+
+    def set_spins(self, spins: np.ndarray, replica: int = 0) -> None:
+        s = np.ascontiguousarray(spins, dtype=np.int8)
+        if s.size != self.N:
+            raise ValueError("spins must hold L^3 values")
+        self._check(lib().ising_set_spins(self._h, replica, s.ctypes.data), "ising_set_spins")
+
+    def get_packed(self, replica: int = 0, out=None, device: bool = False):
+        n = ising_packed_words(self.L)
+        if device:
+            self._check(lib().ising_get_packed(self._h, replica, _dev_ptr(out), PTR_DEVICE), "ising_get_packed")
+            return out
+        if out is None:
+            out = np.empty(n, dtype=np.uint32)
+        _host(out, np.uint32, n, "out")
+        self._check(lib().ising_get_packed(self._h, replica, out.ctypes.data, 0), "ising_get_packed")
+        return out
+
+    def set_packed(self, words, replica: int = 0, device: bool = False) -> None:
+        if device:
+            self._check(lib().ising_set_packed(self._h, replica, _dev_ptr(words), PTR_DEVICE), "ising_set_packed")
+            return
+        w = _host(words, np.uint32, ising_packed_words(self.L), "words")
+        self._check(lib().ising_set_packed(self._h, replica, w.ctypes.data, 0), "ising_set_packed")
+
+    @property
+    def t(self) -> int:
+        v = ctypes.c_int64(0)
+        self._check(lib().ising_get_time(self._h, ctypes.byref(v)), "ising_get_time")
+        return int(v.value)
+
+    @t.setter
+    def t(self, value: int) -> None:
+        self._check(lib().ising_set_time(self._h, value), "ising_set_time")
+
+    def sync(self) -> None:
+        self._check(lib().ising_sync(self._h), "ising_sync")
+
+    def launch_count(self) -> int:
+        return int(lib().ising_launch_count(self._h))
+
+    def destroy(self) -> None:
+        if self._h and self._h.value:
+            lib().ising_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.destroy()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def ising_create(L: int, replicas: int, seed: int, **opts) -> Ising:
+    return Ising(L, replicas, seed, **opts)
+
+
+def ising_sweep(ctx: Ising, n_mcs: int) -> None:
+    ctx.sweep(n_mcs)
+
+
+def ising_measure(ctx: Ising, out: np.ndarray | None = None) -> np.ndarray:
+    return ctx.measure(out)
+
+
+def ising_destroy(ctx: Ising) -> None:
+    ctx.destroy()

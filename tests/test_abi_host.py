@@ -1,0 +1,69 @@
+"""C-ABI checks that need no GPU: the library builds, loads and exports every function
+declared in include/ising.h, and its host-only entry points behave as documented."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared(header):
+    text = open(os.path.join(ROOT, "include", header)).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ising_[a-z_0-9]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2305_12161_gb300 import _build, ising
+    _build.build()
+    return ising.lib()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared("ising.h")
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_record_and_packed_sizes(lib):
+    from paper_2305_12161_gb300 import ising
+    assert ising.ising_record_len(32) == 3 + 3 * 17
+    assert ising.ising_record_len(2048) == 3 + 3 * 1025
+    assert ising.ising_record_len(7) == -1 and ising.ising_record_len(2) == -1
+    assert ising.ising_packed_words(2048) == 2 * 2048 * 2048 * 32
+    assert ising.ising_packed_words(32) == 2 * 32 * 32
+    assert ising.ising_packed_words(4) == 2 * 16
+    assert ising.ising_packed_words(96) == -1  # packed form: multiples of 64 or 4..32
+
+
+def test_strerror_and_variants(lib):
+    from paper_2305_12161_gb300 import ising
+    for code in range(0, -7, -1):
+        assert isinstance(ising.ising_strerror(code), str) and ising.ising_strerror(code)
+    assert ising.ising_variants() == [ising.VARIANT_WORD, ising.VARIANT_ZMARCH]
+
+
+def test_create_rejects_bad_arguments_before_touching_a_device(lib):
+    from paper_2305_12161_gb300 import ising
+    h = ctypes.c_void_p()
+    for L, R in ((7, 1), (2, 1), (96, 1), (64, 0), (8192, 1)):
+        assert lib.ising_create(ctypes.byref(h), L, R, 1) == ising.ISING_EINVAL
+        assert h.value is None
+    assert lib.ising_create(None, 64, 1, 1) == ising.ISING_EINVAL
+    # NULL-safe destroy and NULL-context calls
+    assert lib.ising_destroy(None) == ising.ISING_OK
+    assert lib.ising_sweep(None, 1) == ising.ISING_EINVAL
+    assert lib.ising_measure(None, None) == ising.ISING_EINVAL
+    assert lib.ising_sync(None) == ising.ISING_EINVAL
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    from paper_2305_12161_gb300 import ising
+    monkeypatch.setattr(ising, "_LIB_PATH", str(tmp_path / "nope.so"))
+    monkeypatch.setattr(ising, "_lib", None)
+    with pytest.raises(RuntimeError, match="missing"):
+        ising.lib()

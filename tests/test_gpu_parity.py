@@ -1,0 +1,191 @@
+"""GPU <-> oracle parity through the C ABI (bit-exact: spins and int64 records).
+
+Every case runs the CUDA library and the CPU oracle on the same seeded input and
+compares element by element.  Sizes are chosen so that the oracle finishes in seconds
+while the GPU grids span several tiles (and, for the word variant, a ragged last block).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2305_12161_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+RULES = (0, 1, 2)
+
+
+@pytest.fixture(scope="module")
+def ising():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2305_12161_gb300 import ising as m
+    return m
+
+
+def _run_gpu(ising, L, R, seed, times, keep_spins=True, **opts):
+    recs, spins = [], []
+    with ising.Ising(L, replicas=R, seed=seed, **opts) as q:
+        recs.append(q.measure())
+        if keep_spins:
+            spins.append([q.get_spins(r) for r in range(R)])
+        t = 0
+        for tk in times:
+            q.sweep(tk - t)
+            t = tk
+            recs.append(q.measure())
+            if keep_spins:
+                spins.append([q.get_spins(r) for r in range(R)])
+        assert q.t == t
+    return np.stack(recs, axis=1), spins  # recs: [R, K+1, RL]
+
+
+def _compare(ising, L, R, seed, times, rule=0, **opts):
+    got, gspins = _run_gpu(ising, L, R, seed, times, tie=rule, **opts)
+    for r in range(R):
+        want, ospins = oracle.run(L, seed, r, times, rule=rule, keep_spins=True)
+        for k in range(len(times) + 1):
+            assert np.array_equal(gspins[k][r], ospins[k]), f"spins differ: replica {r}, time index {k}"
+        assert np.array_equal(got[r], want), f"records differ: replica {r}"
+
+
+def test_c1_plain_L32_full_schedule(ising):
+    # smallest instance: one L=32 lattice, seed 1, GLAUBER, 1000 MCS, 20 log-spaced times
+    times = inputs.log_schedule(1000, 20)
+    _compare(ising, 32, 1, 1, times, form=ising.FORM_PLAIN)
+
+
+def test_c1_packed_L32_full_schedule(ising):
+    times = inputs.log_schedule(1000, 20)
+    _compare(ising, 32, 1, 1, times, form=ising.FORM_PACKED)
+
+
+@pytest.mark.parametrize("rule", RULES)
+@pytest.mark.parametrize("L", [4, 8, 16, 64, 128])
+def test_word_variant_small_L_all_rules(ising, L, rule):
+    times = [1, 2, 5, 13, 30]
+    _compare(ising, L, 2, 7, times, rule=rule, variant=ising.VARIANT_WORD)
+
+
+@pytest.mark.parametrize("rule", RULES)
+def test_plain_form_all_rules(ising, rule):
+    _compare(ising, 64, 2, 11, [1, 3, 9, 20], rule=rule, form=ising.FORM_PLAIN)
+
+
+@pytest.mark.parametrize("tiles", [(256, 8), (64, 16), (32, 4), (128, 256)])
+def test_zmarch_L256_vs_oracle(ising, tiles):
+    ty, tz = tiles
+    _compare(ising, 256, 1, 3, [1, 2, 4], variant=ising.VARIANT_ZMARCH, tile_y=ty, tile_z=tz)
+
+
+def test_zmarch_rules_L256(ising):
+    for rule in (1, 2):
+        _compare(ising, 256, 1, 5, [1, 3], rule=rule, variant=ising.VARIANT_ZMARCH)
+
+
+def test_replicas_each_follow_seed_plus_r(ising):
+    _compare(ising, 64, 5, 100, [1, 4, 10])
+
+
+def _packed_state(ising, L, R, seed, n, **opts):
+    with ising.Ising(L, replicas=R, seed=seed, **opts) as q:
+        q.sweep(n)
+        return [q.get_packed(r) for r in range(R)], q.measure()
+
+
+@pytest.mark.parametrize("L", [512, 1024])
+def test_variants_and_tiles_bit_identical(ising, L):
+    ref, rec = _packed_state(ising, L, 1, 9, 6, variant=ising.VARIANT_WORD)
+    W4 = L // 256
+    for ty, tz in ((256 // W4, 32), (128 // W4, 8), (1024 // W4, 64), (32 // W4 if 32 // W4 else 1, L)):
+        if ty * W4 < 32 or ty * W4 > 1024 or L % ty:
+            continue
+        got, grec = _packed_state(ising, L, 1, 9, 6, variant=ising.VARIANT_ZMARCH, tile_y=ty, tile_z=tz)
+        assert np.array_equal(got[0], ref[0]), (ty, tz)
+        assert np.array_equal(grec, rec)
+
+
+def test_plain_and_packed_forms_identical_L256(ising):
+    a, ra = _packed_state(ising, 256, 2, 4, 12, form=ising.FORM_PACKED)
+    b, rb = _packed_state(ising, 256, 2, 4, 12, form=ising.FORM_PLAIN)
+    for r in range(2):
+        assert np.array_equal(a[r], b[r])
+    assert np.array_equal(ra, rb)
+
+
+@pytest.mark.parametrize("L", [4, 16, 32, 64, 128, 256])
+def test_measure_on_structured_states(ising, L):
+    states = [inputs.uniform_state(L, 1), inputs.uniform_state(L, -1), inputs.neel_state(L),
+              inputs.stripe_state(L, max(1, L // 4), "x"), inputs.stripe_state(L, 1, "y", 1),
+              inputs.stripe_state(L, 2, "z"), inputs.random_state(L, 3, 0.3),
+              inputs.cube_defect_state(L, min(L, 3))]
+    with ising.Ising(L, replicas=len(states), seed=1) as q:
+        for r, s in enumerate(states):
+            q.set_spins(s, r)
+        rec, der = q.measure_ex(c=0.5)
+        for r, s in enumerate(states):
+            assert np.array_equal(q.get_spins(r), s)
+            want = oracle.record(s, 0)
+            assert np.array_equal(rec[r], want), r
+            wd = oracle.derived(L, want, 0.5)
+            np.testing.assert_allclose(der[r], wd, rtol=1e-12, atol=0, equal_nan=True)
+        rec2, der2 = q.measure_ex(c=0.4, connected=True)
+        for r, s in enumerate(states):
+            wd = oracle.derived(L, rec2[r], 0.4, connected=True)
+            np.testing.assert_allclose(der2[r], wd, rtol=1e-12, atol=0, equal_nan=True)
+
+
+def test_energy_only_measure_marks_correlations_absent(ising):
+    with ising.Ising(64, replicas=2, seed=3) as q:
+        q.sweep(5)
+        full = q.measure()
+        rec, der = q.measure_ex(corr=False)
+        assert np.array_equal(rec[:, :3], full[:, :3])
+        assert np.all(rec[:, 3:] == -1)
+        assert np.all(np.isnan(der[:, 3]))
+
+
+def test_checkpoint_resume_is_bit_exact(ising):
+    with ising.Ising(256, replicas=1, seed=17) as a:
+        a.sweep(7)
+        ck = a.get_packed(0)
+        t = a.t
+        a.sweep(5)
+        end_a = a.get_packed(0)
+    with ising.Ising(256, replicas=1, seed=17) as b:
+        b.set_packed(ck, 0)
+        b.t = t
+        b.sweep(5)
+        assert np.array_equal(b.get_packed(0), end_a)
+
+
+def test_invalid_spin_values_rejected(ising):
+    with ising.Ising(8, replicas=1, seed=1) as q:
+        bad = np.ones((8, 8, 8), dtype=np.int8)
+        bad[0, 0, 0] = 0
+        with pytest.raises(ising.IsingError):
+            q.set_spins(bad, 0)
+        with pytest.raises(ising.IsingError):
+            q.get_spins(3)
+        # the context is still usable after argument errors
+        q.sweep(1)
+        q.measure()
+
+
+def test_zero_sweeps_and_time(ising):
+    with ising.Ising(64, replicas=1, seed=2) as q:
+        r0 = q.measure()
+        q.sweep(0)
+        assert q.t == 0 and np.array_equal(q.measure(), r0)
+
+
+def test_reinit_equals_fresh_context(ising):
+    with ising.Ising(64, replicas=2, seed=5) as a:
+        a.sweep(9)
+        a.reinit(8)
+        assert a.t == 0
+        a.sweep(3)
+        ra = a.measure()
+    with ising.Ising(64, replicas=2, seed=8) as b:
+        b.sweep(3)
+        assert np.array_equal(b.measure(), ra)

@@ -204,3 +204,18 @@ def test_sweeps_is_red_then_blue_with_sweep_counter():
         oracle.half_sweep(b, 0, t, 4, TIE_GLAUBER)
         oracle.half_sweep(b, 1, t, 4, TIE_GLAUBER)
     assert np.array_equal(a, b)
+
+
+def test_update_sites_matches_full_half_sweep():
+    # the site-by-site entry used for lattices too large for a full oracle pass must
+    # agree with the half-sweep at every listed site
+    L = 16
+    s = oracle.init(L, seed=8)
+    oracle.sweeps(s, 0, 3, 8, TIE_GLAUBER)
+    for q in (0, 1):
+        z, y, x = np.indices((L, L, L))
+        sites = np.flatnonzero(((x + y + z) % 2 == q).ravel())
+        got = oracle.update_sites(s, q, 3, 8, sites)
+        full = s.copy()
+        oracle.half_sweep(full, q, 3, 8, TIE_GLAUBER)
+        assert np.array_equal(got, full.ravel()[sites])
