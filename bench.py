@@ -138,6 +138,19 @@ def run_reference(args):
     }))
 
 
+def run_quench_case(args):
+    """A short plain run of the hot path for ncu: T = infinity start, --mcs sweeps, one
+    full measurement, every kernel launched on the context's stream."""
+    import __graft_entry__
+    from paper_2305_12161_gb300 import ising
+    __graft_entry__.build()
+    with ising.Ising(args.L, replicas=1, seed=1) as q:
+        q.sweep(args.mcs)
+        rec, der = q.measure_ex(c=0.5)
+        print(json.dumps({"case": "quench", "L": args.L, "mcs": args.mcs, "B": int(rec[0, 2]),
+                          "l_E": float(der[0, 2]), "l_C": float(der[0, 3]), "launches": q.launch_count()}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -151,9 +164,14 @@ def main():
     ap.add_argument("--ref-L", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--case", default="bench", choices=["bench", "quench"],
+                    help="quench: init + --mcs sweeps + one measurement, untimed (for profilers)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.case == "quench":
+        run_quench_case(args)
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
