@@ -157,6 +157,30 @@ const char *ising_last_error(const ising_ctx *ctx);
 /* Number of kernel launches this context has enqueued so far (diagnostics). */
 int64_t ising_launch_count(const ising_ctx *ctx);
 
+/* Measurement for callers that cannot allocate device memory (no counterpart in the
+ * paper; it serves library users).  Some callers may not call cudaMalloc where they
+ * measure: code whose device memory is all owned by another allocator or a fixed
+ * arena, or code that must not let an allocation synchronise the device mid-pipeline.
+ * This entry point allocates nothing: the caller passes the packed lattices (device
+ * memory, `replicas` consecutive states in the ising_get_packed layout) and a device
+ * output `derived` of replicas x 4 doubles [e, m, l_E, l_C] (as in ising_measure_ex,
+ * with the same flags except ISING_MEAS_DEVICE, which is implied).  The integer
+ * records it builds on the way live in one fixed array inside the library's device
+ * image, ISING_NOALLOC_MAX_RECORD_WORDS int64 (1 MiB), which every GPU that loads the
+ * library holds until the process exits.
+ *   - Returns ISING_EINVAL when replicas * ising_record_len(L) exceeds that maximum
+ *     (e.g. L = 2048 allows 42 replicas), or for a bad L, pointer or flag.
+ *   - Work is enqueued on `stream` (a cudaStream_t; NULL = the legacy default stream);
+ *     nothing is synchronised.
+ *   - The first call on a device looks up the array's device address (with that device
+ *     current); make that first call before any stream capture.
+ *   - Every call shares the one array, and it keeps the last call's contents (each call
+ *     rewrites what it uses before reading it).  Calls that overlap on the GPU (other
+ *     streams, other host threads) race on it: order them on one stream. */
+#define ISING_NOALLOC_MAX_RECORD_WORDS 131072
+int ising_measure_derived_noalloc(const uint32_t *lattice, int L, int replicas, double c, unsigned flags,
+                                  double *derived, void *stream);
+
 /* Packed sweep kernel variants: fills up to `cap` ids into `ids`, returns the number.
  * Every variant produces bit-identical results; they differ in speed only. */
 int ising_variants(int *ids, int cap);

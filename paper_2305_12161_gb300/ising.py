@@ -80,6 +80,8 @@ def lib() -> ctypes.CDLL:
                 "ising_last_error": (ctypes.c_char_p, [vp]),
                 "ising_launch_count": (ctypes.c_int64, [vp]),
                 "ising_variants": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
+                "ising_measure_derived_noalloc": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                                                 ctypes.c_uint, vp, vp]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -251,6 +253,19 @@ class Ising:
             self.destroy()
         except Exception:
             pass
+
+
+NOALLOC_MAX_RECORD_WORDS = 131072
+
+
+def ising_measure_derived_noalloc(lattice, L: int, replicas: int, derived, c: float = 0.5, connected: bool = False,
+                                  corr: bool = True, stream=None) -> int:
+    """Derived observables of caller-owned packed lattices into a caller-owned device
+    buffer, allocating nothing (for callers that may not allocate device memory).
+    Returns the C status code; the work is enqueued on ``stream`` without a sync."""
+    flags = (MEAS_CONNECTED if connected else 0) | (0 if corr else MEAS_NO_CORR)
+    return int(lib().ising_measure_derived_noalloc(_dev_ptr(lattice), L, replicas, c, flags, _dev_ptr(derived),
+                                                   _stream_handle(stream)))
 
 
 def ising_create(L: int, replicas: int, seed: int, **opts) -> Ising:
