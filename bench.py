@@ -151,6 +151,68 @@ def run_quench_case(args):
                           "l_E": float(der[0, 2]), "l_C": float(der[0, 3]), "launches": q.launch_count()}))
 
 
+BATCH_CLASSES = [(64, 512, 1), (128, 64, 513), (256, 16, 577), (512, 4, 593)]  # seeds 1..596
+
+
+def run_batched(torch, ising, inputs, K: int = 20, window: int = 20) -> dict:
+    """Mixed batch 512x64^3 + 64x128^3 + 16x256^3 + 4x512^3 (each lattice its own seed):
+    the batched form runs 10^4 MCS with K log-spaced measurements as one CUDA graph
+    (persistent launch per segment, work list tuned by the autotuner); the plain form
+    (one byte per spin, one launch per lattice) and the packed form launched per class
+    are compared with it on the same window of `window` MCS from the T = inf start."""
+    stream = torch.cuda.Stream()
+    times = inputs.log_schedule(10_000, K)
+    spins = sum(R * L**3 for L, R, _ in BATCH_CLASSES)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b)
+
+    out = {"workload": "512x64^3 + 64x128^3 + 16x256^3 + 4x512^3, seeds 1..596, 10^4 MCS, "
+                       f"{K} log-spaced measurements (M, B, D_a(r), e, m, l_E, l_C) in one CUDA graph",
+           "spins": spins}
+    with ising.Batch(BATCH_CLASSES, stream=stream) as bt:
+        w = bt.tune(probe_mcs=4)
+        out["autotuner_w_local"] = w
+        out["plan"] = bt.plan()
+        rec = torch.empty((K, bt.record_words), dtype=torch.int64, device="cuda")
+        der = torch.empty((K, bt.lattices, 4), dtype=torch.float64, device="cuda")
+        bt.reinit()
+        bt.run(times, rec=rec, derived=der, device=True)  # capture + warm
+        bt.sync()
+        bt.reinit()
+        l0 = bt.launch_count()
+        ms = timed(lambda: bt.run(times, rec=rec, derived=der, device=True))
+        bt.sync()
+        out["graph_launches"] = bt.launch_count() - l0
+        out["batched_updates_per_ns"] = 10_000 * spins / (ms * 1e-3) / 1e9
+        out["batched_ms"] = ms
+        bt.reinit()
+        bt.sweep(2)
+        bt.reinit()
+        ms_w = timed(lambda: bt.sweep(window))
+        bt.sync()
+        out["window_mcs"] = window
+        out["batched_window_updates_per_ns"] = window * spins / (ms_w * 1e-3) / 1e9
+    for form, key in ((ising.FORM_PLAIN, "plain_window_updates_per_ns"),
+                      (ising.FORM_PACKED, "packed_per_class_window_updates_per_ns")):
+        ctxs = [ising.Ising(L, replicas=R, seed=sd, form=form, stream=stream) for L, R, sd in BATCH_CLASSES]
+        for c in ctxs:
+            c.sweep(1)
+        ms_p = timed(lambda: [c.sweep(window) for c in ctxs])
+        out[key] = window * spins / (ms_p * 1e-3) / 1e9
+        for c in ctxs:
+            c.destroy()
+    out["batched_vs_plain"] = out["batched_window_updates_per_ns"] / out["plain_window_updates_per_ns"]
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -164,6 +226,7 @@ def main():
     ap.add_argument("--ref-L", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--case", default="bench", choices=["bench", "quench"],
                     help="quench: init + --mcs sweeps + one measurement, untimed (for profilers)")
     args = ap.parse_args()
@@ -284,6 +347,10 @@ def main():
         step(True, timing=False)  # warm the host path
         e2e_ms, _ = timed(True, args.steps)
 
+    batched = None
+    if not args.no_batched and rank == 0:
+        batched = run_batched(torch, ising, inputs)
+
     updates_per_step = 2 * MCS * N
     value = world * updates_per_step * args.steps / (ms * 1e-3) / 1e9
 
@@ -299,7 +366,7 @@ def main():
     corr_ops = 3 * (L // 2) * (N // 32)
     n_meas = len(meas_events)
     meas_avg_s = meas_ms * 1e-3 / n_meas
-    popc_peak = 152 * 16 * pk["sm_max_mhz"] * 1e6 / 1e12  # T popc/s: 16 per SM per clock
+    popc_peak = 152 * 16 * pk["sm_max_mhz"] * 1e6 / 1e12  # T popc/s: 16 POPC lanes per SM per clock
     corr_tops = corr_ops / meas_avg_s / 1e12
     roof_sweep = {"kernel": "k_sweep_zmarch (half-sweep)", "bound": "hbm", "achieved": sweep_gbs,
                   "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": sweep_gbs / pk["hbm_gbs"], "traffic": None,
@@ -327,7 +394,7 @@ def main():
             "roofline": roof, "roofline_sweep": roof_sweep, "roofline_measure": roof_corr,
             "breakdown_ms_per_step": {"sweeps": sweep_ms / args.steps, "measurements": meas_ms / args.steps},
             "sweep_only_updates_per_ns": world * (N // 2) / sweep_avg_s / 1e9,
-            "clocks": clk, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clk, "e2e": e2e, "gpu_launches": launches, "batched": batched,
             "cpu_baseline": cpu,
         }
         print(json.dumps(out))

@@ -70,8 +70,11 @@ typedef struct {
     int form;       /* ising_form */
     void *stream;   /* cudaStream_t to enqueue on; NULL: the library creates one */
     int device;     /* CUDA device ordinal; -1: the current device */
-    int variant;    /* packed sweep kernel variant, 0 = automatic (see ising_variants) */
-    int tile_y;     /* packed z-marching variant: rows per tile (0 = automatic) */
+    int variant;    /* packed sweep kernel variant, 0 = automatic (see ising_variants):
+                       1 one thread per word (any L), 2 z-marching tiles (L multiple of 256),
+                       3 z-marching specialised on the row width (L = 256, 512, 1024, 2048) */
+    int tile_y;     /* packed z-marching variant: rows per tile (0 = automatic); variant 3
+                       (z-marching specialised on the row width) fixes it to 256/(L/256) */
     int tile_z;     /* packed z-marching variant: planes per tile (0 = automatic) */
 } ising_opts;
 
@@ -157,6 +160,57 @@ const char *ising_last_error(const ising_ctx *ctx);
 /* Number of kernel launches this context has enqueued so far (diagnostics). */
 int64_t ising_launch_count(const ising_ctx *ctx);
 
+/* ---------------------------------------------------------------------------------
+ * Batched form: many independent lattices of uneven L in one context.  Class c holds
+ * replicas[c] lattices of size L[c], replica r seeded seeds[c] + r, each in its
+ * T = infinity start; all share the sweep counter t.  A segment of n MCS is ONE
+ * persistent cooperative kernel launch over a CTA work list: lattices small enough
+ * for one CTA's shared memory (e.g. 64^3 = 32 KiB packed) are owned whole by one CTA
+ * and swept there; larger ones are split into slabs over a group of CTAs that meet at
+ * a bounded barrier in global memory between half-sweeps.  Every lattice follows
+ * exactly the trajectory of the single-lattice entry points (same rule, order and
+ * random bits), so batching changes speed, not results.
+ * Records and derived values are concatenated in class order, replica-major within a
+ * class: ising_batch_record_words() int64 and 4 * ising_batch_lattices() doubles per
+ * measured time.  Only the PACKED form is batched (opts->form must be PACKED). */
+typedef struct ising_batch ising_batch;
+int ising_batch_create(ising_batch **out, int nclass, const int *L, const int *replicas, const uint64_t *seeds,
+                       const ising_opts *opts);
+/* Enqueue n_mcs sweeps of every lattice: one persistent launch (per 2^30 sweeps). */
+int ising_batch_sweep(ising_batch *b, int64_t n_mcs);
+int64_t ising_batch_record_words(const ising_batch *b);
+int64_t ising_batch_lattices(const ising_batch *b);
+/* Measure every lattice (flags as ising_measure_ex).  Host buffers synchronise and
+ * report a barrier timeout of an earlier segment as ISING_ETIMEOUT. */
+int ising_batch_measure_ex(ising_batch *b, int64_t *rec, double *derived, double c, unsigned flags);
+/* Run a measurement schedule: for k = 0..K-1 sweep to absolute time times[k]
+ * (non-decreasing, >= current t) and measure into slot k of rec (K x record_words) and,
+ * if not NULL, derived (K x 4 x lattices).  The whole schedule (segments and
+ * measurements) is captured into one CUDA graph, which is cached and replayed while the
+ * start time, schedule, flags and output pointers repeat.  ISING_MEAS_DEVICE: device
+ * outputs, no synchronisation; otherwise host outputs and the call synchronises. */
+int ising_batch_run(ising_batch *b, const int64_t *times, int K, int64_t *rec, double *derived, double c,
+                    unsigned flags);
+/* Redraw every lattice's T = infinity start (same seeds) and reset t to 0. */
+int ising_batch_reinit(ising_batch *b);
+int ising_batch_get_packed(ising_batch *b, int cls, int replica, uint32_t *words, unsigned flags);
+int ising_batch_sync(ising_batch *b);
+int ising_batch_get_time(const ising_batch *b, int64_t *t);
+/* Work list summary: CTAs, CTAs owning whole lattices, slab groups, co-resident CTAs. */
+int ising_batch_plan(const ising_batch *b, int *ntasks, int *nlocal, int *ngroups, int *capacity);
+/* Autotuner: probe rounds of probe_mcs sweeps (they advance the batch) time every CTA,
+ * set the relative cost of whole-lattice CTAs from the measured time per spin and
+ * rebuild the work list; *w_local_out receives the chosen weight. */
+int ising_batch_tune(ising_batch *b, int probe_mcs, double *w_local_out);
+int ising_batch_set_weights(ising_batch *b, double w_local, double w_group);
+/* Failure injection for tests: CTA `cta` returns at once, so its slab group's barrier
+ * waits run out after timeout_s; the segment then ends early and the next
+ * synchronising call returns ISING_ETIMEOUT (the batch is poisoned).  cta = -1 clears. */
+int ising_batch_inject_missing_cta(ising_batch *b, int cta, double timeout_s);
+const char *ising_batch_last_error(const ising_batch *b);
+int64_t ising_batch_launch_count(const ising_batch *b);
+int ising_batch_destroy(ising_batch *b);
+
 /* Measurement for callers that cannot allocate device memory (no counterpart in the
  * paper; it serves library users).  Some callers may not call cudaMalloc where they
  * measure: code whose device memory is all owned by another allocator or a fixed
@@ -180,6 +234,15 @@ int64_t ising_launch_count(const ising_ctx *ctx);
 #define ISING_NOALLOC_MAX_RECORD_WORDS 131072
 int ising_measure_derived_noalloc(const uint32_t *lattice, int L, int replicas, double c, unsigned flags,
                                   double *derived, void *stream);
+
+/* Autotuner of the single-lattice sweep: for `replicas` lattices of size L, times
+ * probe_mcs sweeps (after 2 warm-up sweeps) of every valid kernel variant and tile
+ * shape (tile_y rows x tile_z planes per CTA; tile_z sets how many 128-spin words each
+ * thread updates per launch), on scratch contexts built from *base (NULL: defaults),
+ * and writes the fastest options to *best (and its time per MCS in ms).  All
+ * candidates give bit-identical results, so the choice affects speed only. */
+int ising_tune_sweep(int L, int replicas, int probe_mcs, const ising_opts *base, ising_opts *best,
+                     double *best_ms_per_mcs);
 
 /* Packed sweep kernel variants: fills up to `cap` ids into `ids`, returns the number.
  * Every variant produces bit-identical results; they differ in speed only. */

@@ -5,6 +5,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <algorithm>
 #include <vector>
 
 #include "../../include/ising.h"
@@ -131,10 +132,10 @@ int64_t ising_launch_count(const ising_ctx *c) { return c ? c->launches : -1; }
 
 int ising_variants(int *ids, int cap)
 {
-    const int all[2] = {VARIANT_WORD, VARIANT_ZMARCH};
-    if (!ids) return 2;
+    const int all[3] = {VARIANT_WORD, VARIANT_ZMARCH, VARIANT_ZFAST};
+    if (!ids) return 3;
     int n = 0;
-    for (int i = 0; i < 2 && n < cap; ++i) ids[n++] = all[i];
+    for (int i = 0; i < 3 && n < cap; ++i) ids[n++] = all[i];
     return n;
 }
 
@@ -143,11 +144,14 @@ int ising_destroy(ising_ctx *c)
     if (!c) return ISING_OK;
     {
         DeviceGuard dg(c->device);
-        if (c->stream) cudaStreamSynchronize(c->stream);
-        cudaFree(c->lat);
-        cudaFree(c->plain);
-        cudaFree(c->rec_dev);
-        cudaFree(c->der_dev);
+        // stream-ordered frees: releasing a context does not synchronise other streams
+        if (c->stream) {
+            if (c->lat) cudaFreeAsync(c->lat, c->stream);
+            if (c->plain) cudaFreeAsync(c->plain, c->stream);
+            if (c->rec_dev) cudaFreeAsync(c->rec_dev, c->stream);
+            if (c->der_dev) cudaFreeAsync(c->der_dev, c->stream);
+            cudaStreamSynchronize(c->stream);
+        }
         if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     }
     delete c;
@@ -195,24 +199,28 @@ int ising_create_ex(ising_ctx **out, int L, int R, uint64_t seed, const ising_op
         c->cfg = default_sweep_config(L, R);
     } else {
         c->cfg = SweepConfig{o.variant, o.tile_y, o.tile_z};
-        if (c->cfg.variant == VARIANT_ZMARCH && (o.tile_y == 0 || o.tile_z == 0)) {
-            SweepConfig d = default_sweep_config(L, R);
-            if (d.variant == VARIANT_ZMARCH) {
-                if (!o.tile_y) c->cfg.tile_y = d.tile_y;
-                if (!o.tile_z) c->cfg.tile_z = d.tile_z;
+        if ((c->cfg.variant == VARIANT_ZMARCH || c->cfg.variant == VARIANT_ZFAST) && (o.tile_y == 0 || o.tile_z == 0)) {
+            if (L >= 256 && L % 256 == 0) {
+                const int W4 = L / 256;
+                if (!c->cfg.tile_y) c->cfg.tile_y = std::max(1, 256 / W4);
+                if (!c->cfg.tile_z) c->cfg.tile_z = std::min(L, 16);
             }
         }
+        if (c->cfg.variant == VARIANT_ZFAST && L >= 256 && L % 256 == 0) c->cfg.tile_y = 256 / (L / 256);
         if (!sweep_config_valid(L, c->cfg)) return bail(ISING_EINVAL);
     }
+    // stream-ordered allocations (no implicit device synchronisation)
     const size_t pbytes = lattice_bytes_packed(L, R);
-    if (cudaMalloc(&c->lat, pbytes) != cudaSuccess) return bail(ISING_ENOMEM);
+    if (cudaMallocAsync((void **)&c->lat, pbytes, c->stream) != cudaSuccess) return bail(ISING_ENOMEM);
     if (o.form == ISING_FORM_PLAIN) {
         const size_t nbytes = (size_t)R * (size_t)L * L * L;
-        if (cudaMalloc(&c->plain, nbytes) != cudaSuccess) return bail(ISING_ENOMEM);
+        if (cudaMallocAsync((void **)&c->plain, nbytes, c->stream) != cudaSuccess) return bail(ISING_ENOMEM);
     }
-    if (cudaMalloc(&c->rec_dev, sizeof(int64_t) * (size_t)R * ising_record_len(L)) != cudaSuccess)
+    if (cudaMallocAsync((void **)&c->rec_dev, sizeof(int64_t) * (size_t)R * ising_record_len(L), c->stream) !=
+        cudaSuccess)
         return bail(ISING_ENOMEM);
-    if (cudaMalloc(&c->der_dev, sizeof(double) * 4 * (size_t)R) != cudaSuccess) return bail(ISING_ENOMEM);
+    if (cudaMallocAsync((void **)&c->der_dev, sizeof(double) * 4 * (size_t)R, c->stream) != cudaSuccess)
+        return bail(ISING_ENOMEM);
     cudaError_t e;
     if (o.form == ISING_FORM_PLAIN) {
         e = launch_init_plain(c->plain, L, R, seed, c->stream);
@@ -416,6 +424,63 @@ int ising_sync(ising_ctx *c)
     if (s) return s;
     DeviceGuard dg(c->device);
     CK(c, cudaStreamSynchronize(c->stream));
+    return ISING_OK;
+}
+
+int ising_tune_sweep(int L, int replicas, int probe_mcs, const ising_opts *base, ising_opts *best,
+                     double *best_ms_per_mcs)
+{
+    if (!best || probe_mcs < 1 || replicas < 1 || !packed_L_ok(L)) return ISING_EINVAL;
+    ising_opts o;
+    ising_default_opts(&o);
+    if (base) o = *base;
+    if (o.form != ISING_FORM_PACKED) return ISING_EINVAL;
+    std::vector<SweepConfig> cands;
+    cands.push_back(SweepConfig{VARIANT_WORD, 0, 0});
+    const int tzs[] = {4, 8, 16, 32, 64};
+    if (L >= 256 && L % 256 == 0) {
+        const int W4 = L / 256;
+        for (int ty = 1; ty <= L; ty *= 2)
+            for (int tz : tzs) {
+                const SweepConfig c{VARIANT_ZMARCH, ty, tz};
+                if (ty * W4 >= 64 && sweep_config_valid(L, c)) cands.push_back(c);
+            }
+        for (int tz : tzs) {
+            const SweepConfig c{VARIANT_ZFAST, 256 / W4, tz};
+            if (sweep_config_valid(L, c)) cands.push_back(c);
+        }
+    }
+    double best_ms = 1e300;
+    bool found = false;
+    for (const SweepConfig &c : cands) {
+        ising_opts oc = o;
+        oc.variant = c.variant;
+        oc.tile_y = c.tile_y;
+        oc.tile_z = c.tile_z;
+        ising_ctx *ctx = nullptr;
+        int st = ising_create_ex(&ctx, L, replicas, 1, &oc);
+        if (st != ISING_OK) continue;
+        cudaEvent_t a = nullptr, b = nullptr;
+        float ms = 0.f;
+        bool ok = cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess;
+        ok = ok && ising_sweep(ctx, 2) == ISING_OK;
+        ok = ok && cudaEventRecord(a, ctx->stream) == cudaSuccess;
+        ok = ok && ising_sweep(ctx, probe_mcs) == ISING_OK;
+        ok = ok && cudaEventRecord(b, ctx->stream) == cudaSuccess;
+        ok = ok && cudaEventSynchronize(b) == cudaSuccess && cudaEventElapsedTime(&ms, a, b) == cudaSuccess;
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+        ising_destroy(ctx);
+        if (!ok) return ISING_ECUDA;
+        const double per = ms / probe_mcs;
+        if (per < best_ms) {
+            best_ms = per;
+            *best = oc;
+            found = true;
+        }
+    }
+    if (!found) return ISING_EINVAL;
+    if (best_ms_per_mcs) *best_ms_per_mcs = best_ms;
     return ISING_OK;
 }
 

@@ -75,12 +75,16 @@ __global__ void k_mb(const uint32_t *lat, Geom g, int64_t *rec)
 
 // ---------------------------------------------------------------------------------
 // Axis correlation.  blockIdx.z = axis (0 = x, 1 = y, 2 = z), blockIdx.y = replica,
-// blockIdx.x strides over panels of NC columns.
-struct CorrShape {
-    int NC;           // columns per panel
-    int64_t ncols[3]; // columns per replica for each axis
-};
-
+// blockIdx.x strides over panels of NC columns (a persistent grid).
+//
+// A column of L words is staged in shared memory extended to LE = L + NLB*RT words
+// (element j holds col[j mod L]), at padded positions pad(j) = j + j/8 so that the
+// stride-RT window loads below are bank-conflict free.  A work item is (column, block of
+// RT consecutive lags r0..r0+RT-1): the item keeps a register window of the RT partner
+// words col[j + r0 .. j + r0 + RT - 1] and slides it along j, so each step costs one
+// broadcast load (col[j]) and one window load for RT XOR pairs.  The XOR words of each
+// lag are summed by carry-save adders (Harley & Seal's popcount accumulation), which
+// needs one POPC per eight words instead of one per word.
 __host__ __device__ inline int corr_nc(int L)
 {
     int nc = 8192 / L;
@@ -89,18 +93,23 @@ __host__ __device__ inline int corr_nc(int L)
     return nc;
 }
 
+__host__ __device__ inline int corr_rt(int L) { return L >= 8 ? 8 : 4; }
+__host__ __device__ inline int corr_nlb(int L) { return (L / 2 + corr_rt(L) - 1) / corr_rt(L); }
+__host__ __device__ inline int corr_le(int L) { return L + corr_nlb(L) * corr_rt(L); }
+__host__ __device__ inline int corr_pad(int j) { return j + (j >> 3); }
+__host__ __device__ inline int corr_lp(int L) { return corr_pad(corr_le(L) - 1) + 1; }
+
 __host__ __device__ inline int64_t corr_ncols(const Geom &g, int axis)
 {
     if (axis == 0) return ((int64_t)g.L * g.L + 31) / 32;  // 32-row bundles
     return 2 * (int64_t)g.L * g.W;                          // (pi, other coordinate, kw)
 }
 
-// Stage columns c0 .. c0+NC-1 of the y or z axis into sm[c*LE + j], j < L + L/2
-// (column (pi, a, kw): a is z for the y axis, y for the z axis; element j is the other
-// coordinate, wrapped).  Consecutive threads take consecutive columns of one j, which
-// are consecutive words in memory.
+// Stage columns c0 .. c0+NC-1 of the y or z axis (column (pi, a, kw): a is z for the y
+// axis, y for the z axis; element j is the other coordinate).  Consecutive threads take
+// consecutive columns of one j, which are consecutive words in memory.
 __device__ __forceinline__ void load_panel_yz(const uint32_t *S0, const uint32_t *S1, const Geom &g, int axis,
-                                              int64_t c0, int NC, int64_t ncols, uint32_t *sm, int LE,
+                                              int64_t c0, int NC, int64_t ncols, uint32_t *sm, int LE, int LP,
                                               int tid0, int stride)
 {
     const int L = g.L, W = g.W;
@@ -114,30 +123,32 @@ __device__ __forceinline__ void load_panel_yz(const uint32_t *S0, const uint32_t
             const int64_t rem = col - (int64_t)pi * L * W;
             const int a = (int)(rem / W);
             const int kw = (int)(rem - (int64_t)a * W);
-            const int jj = j < L ? j : j - L;
+            int jj = j;
+            while (jj >= L) jj -= L;
             const int y = axis == 1 ? jj : a;
             const int z = axis == 1 ? a : jj;
             const uint32_t *Sq = ((pi + y + z) & 1) ? S1 : S0;
             v = __ldg(Sq + ((int64_t)z * L + y) * W + kw);
         }
-        sm[c * LE + j] = v;
+        sm[c * LP + corr_pad(j)] = v;
     }
 }
 
-template <int NT>
+template <int NT, int RT>
 __global__ void __launch_bounds__(NT) k_corr(const uint32_t *lat, Geom g, int64_t *rec)
 {
     extern __shared__ uint32_t csm[];
     const int axis = blockIdx.z;
     const int r = blockIdx.y;
-    const int L = g.L, H = L / 2, LE = L + L / 2;
+    const int L = g.L, H = L / 2;
+    const int NLB = corr_nlb(L), LE = corr_le(L), LP = corr_lp(L);
     const int NC = corr_nc(L);
     const uint32_t *S0 = lat + (2 * (int64_t)r) * g.nw;
     const uint32_t *S1 = S0 + g.nw;
-    uint32_t *cols = csm;                                           // NC * LE words
-    unsigned long long *acc = reinterpret_cast<unsigned long long *>(csm + ((NC * LE + 1) & ~1));  // H+1
+    uint32_t *cols = csm;  // NC * LP words
+    unsigned long long *acc = reinterpret_cast<unsigned long long *>(csm + ((NC * LP + 1) & ~1));  // NLB*RT+1
     const int tid = threadIdx.x;
-    for (int i = tid; i <= H; i += NT) acc[i] = 0ull;
+    for (int i = tid; i <= NLB * RT; i += NT) acc[i] = 0ull;
     const int64_t ncols = corr_ncols(g, axis);
     const int64_t npanels = (ncols + NC - 1) / NC;
     const int lane = tid & 31, wid = tid >> 5;
@@ -146,9 +157,9 @@ __global__ void __launch_bounds__(NT) k_corr(const uint32_t *lat, Geom g, int64_
         const int64_t c0 = pnl * NC;
         const int nc = (int)min((int64_t)NC, ncols - c0);
         if (axis != 0) {
-            load_panel_yz(S0, S1, g, axis, c0, NC, ncols, cols, LE, tid, NT);
+            load_panel_yz(S0, S1, g, axis, c0, NC, ncols, cols, LE, LP, tid, NT);
         } else {
-            // bundle b = rows 32b .. 32b+31 (row = y + L z); T[x] lane i = site (x, row 32b+i).
+            // bundle = rows 32b .. 32b+31 (row = y + L z); T[x] lane i = site (x, row 32b+i).
             // Tasks: (bundle, pi, kw), one warp each, 32 ballots per task.
             const int ntask = NC * 2 * g.W;
             for (int task = wid; task < ntask; task += NT / 32) {
@@ -169,26 +180,78 @@ __global__ void __launch_bounds__(NT) k_corr(const uint32_t *lat, Geom g, int64_
                 }
                 if (lane < g.RB) {
                     const int x = 2 * (32 * kw + lane) + pi;
-                    cols[c * LE + x] = mine;
-                    if (x < H) cols[c * LE + L + x] = mine;
+                    for (int j = x; j < LE; j += L) cols[c * LP + corr_pad(j)] = mine;
                 }
             }
         }
         __syncthreads();
-        // pairs (column c, lag rr = 1..H): consecutive threads take consecutive lags.
-        const int npairs = NC * H;
-        for (int e = tid; e < npairs; e += NT) {
-            const int c = e / H;
-            const int rr = 1 + (e - c * H);
-            const uint32_t *col = cols + c * LE;
-            unsigned int s = 0;
-            int j = 0;
-            for (; j + 4 <= L; j += 4) {
-                s += __popc(col[j] ^ col[j + rr]) + __popc(col[j + 1] ^ col[j + 1 + rr]) +
-                     __popc(col[j + 2] ^ col[j + 2 + rr]) + __popc(col[j + 3] ^ col[j + 3 + rr]);
+        for (int e = tid; e < NC * NLB; e += NT) {
+            const int c = e / NLB;
+            const int r0 = 1 + (e - c * NLB) * RT;
+            const uint32_t *col = cols + c * LP;
+            uint32_t win[RT];
+#pragma unroll
+            for (int k = 0; k < RT; ++k) win[k] = col[corr_pad(r0 + k)];
+            unsigned int total[RT];
+            if (RT == 8) {
+                // Harley-Seal carry-save accumulation per lag: eight XOR words pass through
+                // seven carry-save adders into (ones, twos, fours) and one "eights" word,
+                // so one POPC covers eight words.
+                uint32_t ones[RT], twos[RT], fours[RT], v[RT], twosA[RT], foursA[RT];
+#pragma unroll
+                for (int k = 0; k < RT; ++k) ones[k] = twos[k] = fours[k] = total[k] = 0u;
+                for (int j = 0; j < L; j += RT) {
+#pragma unroll
+                    for (int u = 0; u < RT; ++u) {
+                        const int jj = j + u;
+                        if (u != 0 || j != 0) win[(u + RT - 1) % RT] = col[corr_pad(r0 + jj + RT - 1)];
+                        const uint32_t a = col[corr_pad(jj)];
+#pragma unroll
+                        for (int k = 0; k < RT; ++k) {
+                            const uint32_t x = a ^ win[(u + k) % RT];
+                            if ((u & 1) == 0) {
+                                v[k] = x;
+                            } else {
+                                // (carry, sum) of ones + v + x
+                                const uint32_t t2 = (ones[k] & v[k]) | (x & (ones[k] ^ v[k]));
+                                ones[k] = ones[k] ^ v[k] ^ x;
+                                if (u == 1 || u == 5) {
+                                    twosA[k] = t2;
+                                } else {
+                                    const uint32_t t4 = (twos[k] & twosA[k]) | (t2 & (twos[k] ^ twosA[k]));
+                                    twos[k] = twos[k] ^ twosA[k] ^ t2;
+                                    if (u == 3) {
+                                        foursA[k] = t4;
+                                    } else {
+                                        const uint32_t t8 = (fours[k] & foursA[k]) | (t4 & (fours[k] ^ foursA[k]));
+                                        fours[k] = fours[k] ^ foursA[k] ^ t4;
+                                        total[k] += __popc(t8);
+                                    }
+                                }
+                            }
+                        }
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < RT; ++k)
+                    total[k] = 8u * total[k] + 4u * __popc(fours[k]) + 2u * __popc(twos[k]) + __popc(ones[k]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < RT; ++k) total[k] = 0u;
+                for (int j = 0; j < L; j += RT) {
+#pragma unroll
+                    for (int u = 0; u < RT; ++u) {
+                        const int jj = j + u;
+                        if (u != 0 || j != 0) win[(u + RT - 1) % RT] = col[corr_pad(r0 + jj + RT - 1)];
+                        const uint32_t a = col[corr_pad(jj)];
+#pragma unroll
+                        for (int k = 0; k < RT; ++k) total[k] += __popc(a ^ win[(u + k) % RT]);
+                    }
+                }
             }
-            for (; j < L; ++j) s += __popc(col[j] ^ col[j + rr]);
-            atomicAdd(acc + rr, (unsigned long long)s);
+#pragma unroll
+            for (int k = 0; k < RT; ++k)
+                if (total[k]) atomicAdd(acc + r0 + k, (unsigned long long)total[k]);
         }
     }
     __syncthreads();
@@ -200,8 +263,32 @@ __global__ void __launch_bounds__(NT) k_corr(const uint32_t *lat, Geom g, int64_
 static size_t corr_smem(int L)
 {
     const int NC = corr_nc(L);
-    const size_t words = ((size_t)NC * (L + L / 2) + 1) & ~(size_t)1;
-    return words * 4 + (size_t)(L / 2 + 1) * 8;
+    const size_t words = ((size_t)NC * corr_lp(L) + 1) & ~(size_t)1;
+    return words * 4 + (size_t)(corr_nlb(L) * corr_rt(L) + 1) * 8;
+}
+
+template <int RT>
+static cudaError_t launch_corr(const uint32_t *lat, const Geom &g, int R, int64_t *rec, cudaStream_t s)
+{
+    const int L = g.L;
+    const size_t smem = corr_smem(L);
+    cudaError_t e = cudaFuncSetAttribute(k_corr<256, RT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, occ = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_corr<256, RT>, 256, smem)) != cudaSuccess) return e;
+    if (occ < 1) occ = 1;
+    int64_t maxc = corr_ncols(g, 0);
+    if (corr_ncols(g, 1) > maxc) maxc = corr_ncols(g, 1);
+    const int NC = corr_nc(L);
+    int64_t panels = (maxc + NC - 1) / NC;
+    // persistent: one resident wave over the 3 axes and R replicas
+    int64_t want = ((int64_t)occ * sms) / ((int64_t)3 * R);
+    if (want < 1) want = 1;
+    if (panels > want) panels = want;
+    k_corr<256, RT><<<dim3((unsigned)panels, (unsigned)R, 3), 256, smem, s>>>(lat, g, rec);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_measure(const uint32_t *lat, int L, int R, int64_t t, bool corr, int64_t *rec, cudaStream_t s,
@@ -217,23 +304,8 @@ cudaError_t launch_measure(const uint32_t *lat, int L, int R, int64_t t, bool co
     k_mb<<<dim3((unsigned)mb, (unsigned)R), 256, 0, s>>>(lat, g, rec);
     int n = 2;
     if (corr) {
-        const size_t smem = corr_smem(L);
-        cudaError_t e = cudaFuncSetAttribute(k_corr<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        const cudaError_t e = corr_rt(L) == 8 ? launch_corr<8>(lat, g, R, rec, s) : launch_corr<4>(lat, g, R, rec, s);
         if (e != cudaSuccess) return e;
-        int dev = 0, sms = 0, occ = 0;
-        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_corr<256>, 256, smem)) != cudaSuccess) return e;
-        if (occ < 1) occ = 1;
-        int64_t maxc = corr_ncols(g, 0);
-        if (corr_ncols(g, 1) > maxc) maxc = corr_ncols(g, 1);
-        const int NC = corr_nc(L);
-        int64_t panels = (maxc + NC - 1) / NC;
-        // persistent: one resident wave over the 3 axes and R replicas
-        int64_t want = ((int64_t)occ * sms) / ((int64_t)3 * R);
-        if (want < 1) want = 1;
-        if (panels > want) panels = want;
-        k_corr<256><<<dim3((unsigned)panels, (unsigned)R, 3), 256, smem, s>>>(lat, g, rec);
         ++n;
     }
     if (launches) *launches += n;

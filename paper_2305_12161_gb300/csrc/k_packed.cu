@@ -210,9 +210,123 @@ __global__ void __launch_bounds__(1024) k_sweep_zmarch(uint32_t *lat, Geom g, in
 }
 
 // ---------------------------------------------------------------------------------
+// ZFAST variant: the z-marching scheme specialised on the row width W4 (uint4 per row)
+// with 256 threads, so a tile is TY = 256 / W4 full rows and all index arithmetic is
+// compile-time.  Per plane each thread reads one new other-sublattice word of its own
+// column (z+1) and keeps z-1 and z in registers; the y-neighbours and the x edge come
+// from the shared ring; its own-sublattice word is prefetched from global memory two
+// planes ahead into registers.  Philox round keys are computed once per thread.
+template <int RULE, int W4>
+__global__ void __launch_bounds__(256) k_sweep_zfast(uint32_t *lat, Geom g, int q, uint32_t t, uint64_t seed, int TZ)
+{
+    constexpr int NT = 256, TY = NT / W4;
+    constexpr int OSZ = (TY + 2) * W4;  // uint4 per ring slot: the tile and one halo row each side
+    constexpr int NS = 5;               // slots: planes z, z+1 being read, z+2, z+3 in flight, 1 spare
+    __shared__ uint4 ring[NS * OSZ];
+    const int L = g.L;
+    const int tid = threadIdx.x;
+    const int ty = tid / W4, cx = tid % W4;
+    const int nty = L / TY;
+    const int y0 = (int)(blockIdx.x % nty) * TY;
+    const int z0 = (int)(blockIdx.x / nty) * TZ;
+    const int r = blockIdx.y;
+    uint4 *S4 = reinterpret_cast<uint4 *>(lat + (2 * (int64_t)r + q) * g.nw);
+    const uint4 *O4 = reinterpret_cast<const uint4 *>(lat + (2 * (int64_t)r + (1 - q)) * g.nw);
+    const PhiloxKeys keys = philox_keys(seed + (uint64_t)r);
+    const int64_t plane4 = (int64_t)L * W4;
+
+    // copy sources of this thread inside a plane: ring row ty <- global row y0-1+ty, and
+    // for tid < 2*W4 ring row TY+tid/W4 <- global row y0-1+TY+tid/W4
+    int ya = y0 - 1 + ty;
+    ya = ya < 0 ? ya + L : ya;
+    const int64_t offa = (int64_t)ya * W4 + cx;
+    const bool halo = tid < 2 * W4;
+    int yb = y0 - 1 + TY + ty;  // ty is 0 or 1 here
+    yb = yb >= L ? yb - L : yb;
+    const int64_t offb = (int64_t)yb * W4 + cx;
+    const int y = y0 + ty;
+    const int64_t own = (int64_t)y * W4 + cx;  // own column within a plane
+
+    auto issue = [&](int gi) {  // other-sublattice plane z0-1+gi into slot gi % NS
+        if (gi <= TZ + 1) {
+            int pz = z0 - 1 + gi;
+            pz = pz < 0 ? pz + L : (pz >= L ? pz - L : pz);
+            const uint4 *src = O4 + (int64_t)pz * plane4;
+            uint4 *dst = ring + (gi % NS) * OSZ;
+            cp_async16(dst + tid, src + offa);
+            if (halo) cp_async16(dst + NT + tid, src + offb);
+        }
+        cp_async_commit();
+    };
+
+#pragma unroll 1
+    for (int gi = 0; gi < 4; ++gi) issue(gi);
+    uint4 sA = S4[(int64_t)z0 * plane4 + own];
+    uint4 sB = TZ > 1 ? S4[(int64_t)(z0 + 1) * plane4 + own] : sA;
+    cp_async_wait<2>();  // groups 0 and 1 (planes z0-1, z0) have landed
+    __syncthreads();
+    uint4 cm = ring[0 * OSZ + (ty + 1) * W4 + cx];  // plane z-1, own column
+    uint4 cc = ring[1 * OSZ + (ty + 1) * W4 + cx];  // plane z
+    const int cxl = (cx + W4 - 1) % W4, cxr = (cx + 1) % W4;
+    int sz = 1;  // slot of plane z
+#pragma unroll 1
+    for (int i = 0; i < TZ; ++i) {
+        cp_async_wait<1>();  // group i+2 (plane z+1) has landed
+        __syncthreads();
+        issue(i + 4);        // overwrites the slot of plane z-2, last read in step i-1
+        const int z = z0 + i;
+        const int szp = sz == NS - 1 ? 0 : sz + 1;
+        const uint4 *Oz = ring + sz * OSZ;
+        const uint4 cp = ring[szp * OSZ + (ty + 1) * W4 + cx];
+        const uint4 ym = Oz[ty * W4 + cx];
+        const uint4 yp = Oz[(ty + 2) * W4 + cx];
+        const uint4 s = sA;
+        sA = sB;
+        if (i + 2 < TZ) sB = S4[(int64_t)(z + 2) * plane4 + own];
+        const int p = (y + z + q) & 1;
+        uint4 X;
+        if (p == 0) {
+            const uint32_t e = Oz[(ty + 1) * W4 + cxl].w;
+            X.x = __funnelshift_l(e, cc.x, 1);
+            X.y = __funnelshift_l(cc.x, cc.y, 1);
+            X.z = __funnelshift_l(cc.y, cc.z, 1);
+            X.w = __funnelshift_l(cc.z, cc.w, 1);
+        } else {
+            const uint32_t e = Oz[(ty + 1) * W4 + cxr].x;
+            X.x = __funnelshift_r(cc.x, cc.y, 1);
+            X.y = __funnelshift_r(cc.y, cc.z, 1);
+            X.z = __funnelshift_r(cc.z, cc.w, 1);
+            X.w = __funnelshift_r(cc.w, e, 1);
+        }
+        uint32_t g0, g1, g2, g3, e0, e1, e2, e3;
+        count6(cc.x, X.x, ym.x, yp.x, cm.x, cp.x, g0, e0);
+        count6(cc.y, X.y, ym.y, yp.y, cm.y, cp.y, g1, e1);
+        count6(cc.z, X.z, ym.z, yp.z, cm.z, cp.z, g2, e2);
+        count6(cc.w, X.w, ym.w, yp.w, cm.w, cp.w, g3, e3);
+        const uint32_t gidx = (uint32_t)((int64_t)z * plane4 + own);  // Philox group = word >> 2
+        U4 o{0u, 0u, 0u, 0u};
+        if (RULE == TIE_GLAUBER && (e0 | e1 | e2 | e3) != 0u) o = philox4x32_10_rk(gidx, t, (uint32_t)q, 0u, keys);
+        uint4 nw;
+        nw.x = resolve<RULE>(s.x, g0, e0, o.x);
+        nw.y = resolve<RULE>(s.y, g1, e1, o.y);
+        nw.z = resolve<RULE>(s.z, g2, e2, o.z);
+        nw.w = resolve<RULE>(s.w, g3, e3, o.w);
+        S4[(int64_t)z * plane4 + own] = nw;
+        cm = cc;
+        cc = cp;
+        sz = szp;
+    }
+    cp_async_wait<0>();
+}
+
+// ---------------------------------------------------------------------------------
+static bool zfast_width_ok(int L) { return L % 256 == 0 && (L / 256 == 1 || L / 256 == 2 || L / 256 == 4 || L / 256 == 8); }
+
 bool sweep_config_valid(int L, const SweepConfig &c)
 {
     if (c.variant == VARIANT_WORD) return true;
+    if (c.variant == VARIANT_ZFAST)
+        return L >= 256 && zfast_width_ok(L) && c.tile_z >= 1 && L % c.tile_z == 0 && L % (256 / (L / 256)) == 0;
     if (c.variant != VARIANT_ZMARCH) return false;
     if (L < 256 || L % 256 != 0) return false;
     const int W4 = L / 256;
@@ -236,6 +350,13 @@ SweepConfig default_sweep_config(int L, int R)
         while (tz > 4 && (int64_t)(L / ty) * (L / tz) * R < 4 * 152) tz >>= 1;
         c = SweepConfig{VARIANT_ZMARCH, ty, tz};
         if (!sweep_config_valid(L, c)) c = SweepConfig{VARIANT_WORD, 0, 0};
+        if (zfast_width_ok(L)) {
+            const int fty = 256 / W4;
+            int ftz = 32;
+            while (ftz > 4 && (int64_t)(L / fty) * (L / ftz) * R < 4 * 152) ftz >>= 1;
+            const SweepConfig f{VARIANT_ZFAST, fty, ftz};
+            if (sweep_config_valid(L, f)) c = f;
+        }
     }
     return c;
 }
@@ -245,7 +366,21 @@ static cudaError_t sweeps_rule(uint32_t *lat, int L, int R, uint64_t seed, int64
                                const SweepConfig &cfg, cudaStream_t s, int64_t *launches)
 {
     const Geom g = make_geom(L);
-    if (cfg.variant == VARIANT_ZMARCH) {
+    if (cfg.variant == VARIANT_ZFAST) {
+        const int W4 = L / 256;
+        const dim3 grid((unsigned)((L / (256 / W4)) * (L / cfg.tile_z)), (unsigned)R);
+        for (int64_t k = 0; k < n; ++k) {
+            const uint32_t t = (uint32_t)(t0 + k);
+            for (int q = 0; q < 2; ++q) {
+                switch (W4) {
+                case 1: k_sweep_zfast<RULE, 1><<<grid, 256, 0, s>>>(lat, g, q, t, seed, cfg.tile_z); break;
+                case 2: k_sweep_zfast<RULE, 2><<<grid, 256, 0, s>>>(lat, g, q, t, seed, cfg.tile_z); break;
+                case 4: k_sweep_zfast<RULE, 4><<<grid, 256, 0, s>>>(lat, g, q, t, seed, cfg.tile_z); break;
+                default: k_sweep_zfast<RULE, 8><<<grid, 256, 0, s>>>(lat, g, q, t, seed, cfg.tile_z); break;
+                }
+            }
+        }
+    } else if (cfg.variant == VARIANT_ZMARCH) {
         const int W4 = L / 256;
         const size_t smem = zmarch_smem_bytes(L, cfg.tile_y);
         static bool attr_set = false;  // idempotent; benign if repeated

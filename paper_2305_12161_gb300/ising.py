@@ -26,7 +26,7 @@ TIE_GLAUBER, TIE_ALWAYS, TIE_NEVER = 0, 1, 2
 FORM_PACKED, FORM_PLAIN = 0, 1
 MEAS_DEVICE, MEAS_CONNECTED, MEAS_NO_CORR = 1, 2, 4
 PTR_DEVICE = 1
-VARIANT_AUTO, VARIANT_WORD, VARIANT_ZMARCH = 0, 1, 2
+VARIANT_AUTO, VARIANT_WORD, VARIANT_ZMARCH, VARIANT_ZFAST = 0, 1, 2, 3
 
 
 class IsingError(RuntimeError):
@@ -80,6 +80,27 @@ def lib() -> ctypes.CDLL:
                 "ising_last_error": (ctypes.c_char_p, [vp]),
                 "ising_launch_count": (ctypes.c_int64, [vp]),
                 "ising_variants": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
+                "ising_tune_sweep": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                    ctypes.POINTER(ising_opts), ctypes.POINTER(ising_opts),
+                                                    ctypes.POINTER(ctypes.c_double)]),
+                "ising_batch_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, vp, vp, vp,
+                                                      ctypes.POINTER(ising_opts)]),
+                "ising_batch_sweep": (ctypes.c_int, [vp, ctypes.c_int64]),
+                "ising_batch_record_words": (ctypes.c_int64, [vp]),
+                "ising_batch_lattices": (ctypes.c_int64, [vp]),
+                "ising_batch_measure_ex": (ctypes.c_int, [vp, vp, vp, ctypes.c_double, ctypes.c_uint]),
+                "ising_batch_run": (ctypes.c_int, [vp, vp, ctypes.c_int, vp, vp, ctypes.c_double, ctypes.c_uint]),
+                "ising_batch_reinit": (ctypes.c_int, [vp]),
+                "ising_batch_get_packed": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_uint]),
+                "ising_batch_sync": (ctypes.c_int, [vp]),
+                "ising_batch_get_time": (ctypes.c_int, [vp, i64p]),
+                "ising_batch_plan": (ctypes.c_int, [vp, vp, vp, vp, vp]),
+                "ising_batch_tune": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+                "ising_batch_set_weights": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_double]),
+                "ising_batch_inject_missing_cta": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_double]),
+                "ising_batch_last_error": (ctypes.c_char_p, [vp]),
+                "ising_batch_launch_count": (ctypes.c_int64, [vp]),
+                "ising_batch_destroy": (ctypes.c_int, [vp]),
                 "ising_measure_derived_noalloc": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                                                  ctypes.c_uint, vp, vp]),
             }
@@ -240,6 +261,144 @@ class Ising:
     def destroy(self) -> None:
         if self._h and self._h.value:
             lib().ising_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.destroy()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def ising_tune_sweep(L: int, replicas: int = 1, probe_mcs: int = 8, tie: int = TIE_GLAUBER) -> dict:
+    """Fastest (variant, tile_y, tile_z) for this size; pass them to Ising(...)."""
+    base = ising_opts()
+    lib().ising_default_opts(ctypes.byref(base))
+    base.tie = tie
+    best = ising_opts()
+    ms = ctypes.c_double(0)
+    st = lib().ising_tune_sweep(L, replicas, probe_mcs, ctypes.byref(base), ctypes.byref(best), ctypes.byref(ms))
+    if st != ISING_OK:
+        raise IsingError(st, "ising_tune_sweep")
+    return {"variant": best.variant, "tile_y": best.tile_y, "tile_z": best.tile_z, "ms_per_mcs": ms.value}
+
+
+class Batch:
+    """Lattice classes [(L, replicas, seed), ...] advanced together by one persistent
+    launch per segment (see ``ising_batch_*`` in include/ising.h)."""
+
+    def __init__(self, classes, tie: int = TIE_GLAUBER, stream=None, device: int = -1):
+        self._h = ctypes.c_void_p()
+        self.classes = [(int(L), int(R), int(s)) for L, R, s in classes]
+        n = len(self.classes)
+        Ls = (ctypes.c_int * n)(*[c[0] for c in self.classes])
+        Rs = (ctypes.c_int * n)(*[c[1] for c in self.classes])
+        Ss = (ctypes.c_uint64 * n)(*[c[2] % 2**64 for c in self.classes])
+        o = ising_opts()
+        lib().ising_default_opts(ctypes.byref(o))
+        o.tie, o.device = tie, device
+        sh = _stream_handle(stream)
+        o.stream = sh if sh else None
+        self._stream_obj = stream
+        st = lib().ising_batch_create(ctypes.byref(self._h), n, ctypes.cast(Ls, ctypes.c_void_p),
+                                      ctypes.cast(Rs, ctypes.c_void_p), ctypes.cast(Ss, ctypes.c_void_p),
+                                      ctypes.byref(o))
+        if st != ISING_OK:
+            raise IsingError(st, "ising_batch_create")
+        self.record_words = int(lib().ising_batch_record_words(self._h))
+        self.lattices = int(lib().ising_batch_lattices(self._h))
+        self.offsets = []  # (record offset, derived row offset) per class
+        ro = do = 0
+        for L, R, _ in self.classes:
+            self.offsets.append((ro, do))
+            ro += R * ising_record_len(L)
+            do += R
+
+    def _check(self, st: int, where: str) -> None:
+        if st != ISING_OK:
+            detail = lib().ising_batch_last_error(self._h) if self._h else b""
+            raise IsingError(st, where, (detail or b"").decode())
+
+    def sweep(self, n_mcs: int) -> None:
+        self._check(lib().ising_batch_sweep(self._h, n_mcs), "ising_batch_sweep")
+
+    def measure_ex(self, c: float = 0.5, connected: bool = False, corr: bool = True):
+        rec = np.empty(self.record_words, dtype=np.int64)
+        der = np.empty((self.lattices, 4), dtype=np.float64)
+        flags = (MEAS_CONNECTED if connected else 0) | (0 if corr else MEAS_NO_CORR)
+        self._check(lib().ising_batch_measure_ex(self._h, rec.ctypes.data, der.ctypes.data, c, flags),
+                    "ising_batch_measure_ex")
+        return rec, der
+
+    def run(self, times, c: float = 0.5, connected: bool = False, corr: bool = True, rec=None, derived=None,
+            device: bool = False):
+        """Schedule run (one CUDA graph).  Host mode returns (rec [K, words], der [K, lat, 4])."""
+        t = np.ascontiguousarray(times, dtype=np.int64)
+        K = t.size
+        flags = (MEAS_CONNECTED if connected else 0) | (0 if corr else MEAS_NO_CORR)
+        if device:
+            flags |= MEAS_DEVICE
+            dp = _dev_ptr(derived) if derived is not None else None
+            self._check(lib().ising_batch_run(self._h, t.ctypes.data, K, _dev_ptr(rec), dp, c, flags),
+                        "ising_batch_run")
+            return rec, derived
+        rec = np.empty((K, self.record_words), dtype=np.int64)
+        der = np.empty((K, self.lattices, 4), dtype=np.float64)
+        self._check(lib().ising_batch_run(self._h, t.ctypes.data, K, rec.ctypes.data, der.ctypes.data, c, flags),
+                    "ising_batch_run")
+        return rec, der
+
+    def record_of(self, rec_block: np.ndarray, cls: int, replica: int) -> np.ndarray:
+        """One lattice's record out of a batch record block."""
+        L, R, _ = self.classes[cls]
+        off = self.offsets[cls][0] + replica * ising_record_len(L)
+        return rec_block[off:off + ising_record_len(L)]
+
+    def reinit(self) -> None:
+        self._check(lib().ising_batch_reinit(self._h), "ising_batch_reinit")
+
+    def get_packed(self, cls: int, replica: int) -> np.ndarray:
+        out = np.empty(ising_packed_words(self.classes[cls][0]), dtype=np.uint32)
+        self._check(lib().ising_batch_get_packed(self._h, cls, replica, out.ctypes.data, 0), "ising_batch_get_packed")
+        return out
+
+    def sync(self) -> None:
+        self._check(lib().ising_batch_sync(self._h), "ising_batch_sync")
+
+    @property
+    def t(self) -> int:
+        v = ctypes.c_int64(0)
+        self._check(lib().ising_batch_get_time(self._h, ctypes.byref(v)), "ising_batch_get_time")
+        return int(v.value)
+
+    def plan(self) -> dict:
+        v = [ctypes.c_int(0) for _ in range(4)]
+        self._check(lib().ising_batch_plan(self._h, *[ctypes.byref(x) for x in v]), "ising_batch_plan")
+        return dict(zip(("ctas", "local_ctas", "groups", "capacity"), (x.value for x in v)))
+
+    def tune(self, probe_mcs: int = 4) -> float:
+        w = ctypes.c_double(0)
+        self._check(lib().ising_batch_tune(self._h, probe_mcs, ctypes.byref(w)), "ising_batch_tune")
+        return float(w.value)
+
+    def set_weights(self, w_local: float, w_group: float = 1.0) -> None:
+        self._check(lib().ising_batch_set_weights(self._h, w_local, w_group), "ising_batch_set_weights")
+
+    def inject_missing_cta(self, cta: int, timeout_s: float = 1.0) -> None:
+        self._check(lib().ising_batch_inject_missing_cta(self._h, cta, timeout_s), "ising_batch_inject_missing_cta")
+
+    def launch_count(self) -> int:
+        return int(lib().ising_batch_launch_count(self._h))
+
+    def destroy(self) -> None:
+        if self._h and self._h.value:
+            lib().ising_batch_destroy(self._h)
             self._h = ctypes.c_void_p()
 
     def __enter__(self):

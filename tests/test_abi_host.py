@@ -44,7 +44,7 @@ def test_strerror_and_variants(lib):
     from paper_2305_12161_gb300 import ising
     for code in range(0, -7, -1):
         assert isinstance(ising.ising_strerror(code), str) and ising.ising_strerror(code)
-    assert ising.ising_variants() == [ising.VARIANT_WORD, ising.VARIANT_ZMARCH]
+    assert ising.ising_variants() == [ising.VARIANT_WORD, ising.VARIANT_ZMARCH, ising.VARIANT_ZFAST]
 
 
 def test_create_rejects_bad_arguments_before_touching_a_device(lib):
@@ -67,3 +67,19 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(ising, "_lib", None)
     with pytest.raises(RuntimeError, match="missing"):
         ising.lib()
+
+
+def test_batch_create_rejects_bad_arguments(lib):
+    from paper_2305_12161_gb300 import ising
+    h = ctypes.c_void_p()
+
+    def arr(t, v):
+        a = (t * len(v))(*v)
+        return ctypes.cast(a, ctypes.c_void_p), a
+
+    for Ls, Rs in (([96], [1]), ([64, 7], [1, 1]), ([64], [0])):
+        (pl, a), (pr, b), (ps, c) = arr(ctypes.c_int, Ls), arr(ctypes.c_int, Rs), arr(ctypes.c_uint64, [1] * len(Ls))
+        assert lib.ising_batch_create(ctypes.byref(h), len(Ls), pl, pr, ps, None) == ising.ISING_EINVAL
+    assert lib.ising_batch_create(ctypes.byref(h), 0, None, None, None, None) == ising.ISING_EINVAL
+    assert lib.ising_batch_destroy(None) == ising.ISING_OK
+    assert lib.ising_batch_sweep(None, 1) == ising.ISING_EINVAL

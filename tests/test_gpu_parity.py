@@ -78,6 +78,17 @@ def test_zmarch_L256_vs_oracle(ising, tiles):
     _compare(ising, 256, 1, 3, [1, 2, 4], variant=ising.VARIANT_ZMARCH, tile_y=ty, tile_z=tz)
 
 
+@pytest.mark.parametrize("tz", [1, 4, 16, 256])
+def test_zfast_L256_vs_oracle(ising, tz):
+    _compare(ising, 256, 1, 13, [1, 2, 5], variant=ising.VARIANT_ZFAST, tile_z=tz)
+
+
+def test_zfast_rules_and_replicas_L256(ising):
+    for rule in (1, 2):
+        _compare(ising, 256, 1, 6, [1, 3], rule=rule, variant=ising.VARIANT_ZFAST)
+    _compare(ising, 256, 2, 21, [2], variant=ising.VARIANT_ZFAST, tile_z=8)
+
+
 def test_zmarch_rules_L256(ising):
     for rule in (1, 2):
         _compare(ising, 256, 1, 5, [1, 3], rule=rule, variant=ising.VARIANT_ZMARCH)
@@ -93,7 +104,7 @@ def _packed_state(ising, L, R, seed, n, **opts):
         return [q.get_packed(r) for r in range(R)], q.measure()
 
 
-@pytest.mark.parametrize("L", [512, 1024])
+@pytest.mark.parametrize("L", [512, 1024, 2048])
 def test_variants_and_tiles_bit_identical(ising, L):
     ref, rec = _packed_state(ising, L, 1, 9, 6, variant=ising.VARIANT_WORD)
     W4 = L // 256
@@ -102,6 +113,10 @@ def test_variants_and_tiles_bit_identical(ising, L):
             continue
         got, grec = _packed_state(ising, L, 1, 9, 6, variant=ising.VARIANT_ZMARCH, tile_y=ty, tile_z=tz)
         assert np.array_equal(got[0], ref[0]), (ty, tz)
+        assert np.array_equal(grec, rec)
+    for tz in (2, 32, L):
+        got, grec = _packed_state(ising, L, 1, 9, 6, variant=ising.VARIANT_ZFAST, tile_z=tz)
+        assert np.array_equal(got[0], ref[0]), ("zfast", tz)
         assert np.array_equal(grec, rec)
 
 

@@ -1,0 +1,42 @@
+"""Serving loop: requests that overlap on the device give the same result as alone."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def serve():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2305_12161_gb300 import serve as m
+    return m
+
+
+def test_mix_equals_alone_and_admission_respects_budget(serve):
+    reqs = [serve.Request(id=0, L=64, t_max=300, replicas=3, seed=11, arrival_s=0.0, K=6),
+            serve.Request(id=1, L=128, t_max=120, replicas=2, seed=22, arrival_s=0.0, K=5),
+            serve.Request(id=2, L=256, t_max=80, replicas=1, seed=33, arrival_s=0.01, K=4),
+            serve.Request(id=3, L=64, t_max=50, replicas=16, seed=44, arrival_s=0.02, K=5),
+            serve.Request(id=4, L=512, t_max=20, replicas=1, seed=55, arrival_s=0.03, K=3)]
+    # a budget that holds only some requests at once forces queueing on memory
+    budget = serve.footprint_bytes(512, 1, 3) + serve.footprint_bytes(256, 1, 4) + 1
+    srv = serve.QuenchServer(budget_bytes=budget, max_slots=3, quantum_mcs=16)
+    results = {r.request.id: r for r in srv.run(reqs)}
+    assert sorted(results) == [0, 1, 2, 3, 4]
+    assert srv.used == 0
+    for req in reqs:
+        alone = serve.run_alone(req)
+        got = results[req.id]
+        assert got.times == alone.times
+        assert np.array_equal(got.records, alone.records), req.id
+        np.testing.assert_allclose(got.derived, alone.derived, rtol=1e-12, atol=0, equal_nan=True)
+        assert got.records[-1, 0, 0] == req.t_max
+    s = srv.summary()
+    assert s["requests"] == 5 and s["p99_s"] >= s["p50_s"] > 0 and s["updates_per_ns"] > 0
+
+
+def test_oversized_request_rejected(serve):
+    srv = serve.QuenchServer(budget_bytes=1e6)
+    with pytest.raises(ValueError):
+        srv.submit(serve.Request(id=0, L=256, t_max=10, replicas=1, seed=1))
