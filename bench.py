@@ -213,6 +213,59 @@ def run_batched(torch, ising, inputs, K: int = 20, window: int = 20) -> dict:
     return out
 
 
+def aggregate_ranks(ms: float, updates: float, dist=None, device=None) -> tuple[float, float]:
+    """Whole-job numbers over ranks: the slowest rank's time (MAX) and the units all
+    ranks processed (SUM).  Without a process group, the local numbers."""
+    if dist is None:
+        return ms, updates
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    u = torch.tensor([updates], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+def run_batch_case(args):
+    """A short plain run of the batched form for ncu: the mixed batch, --mcs sweeps in one
+    persistent launch, then one measurement of every lattice."""
+    import __graft_entry__
+    from paper_2305_12161_gb300 import ising
+    __graft_entry__.build()
+    with ising.Batch(BATCH_CLASSES) as b:
+        b.sweep(args.mcs)
+        rec, der = b.measure_ex()
+        print(json.dumps({"case": "batch", "mcs": args.mcs, "plan": b.plan(), "launches": b.launch_count()}))
+
+
+def run_serve_case(args):
+    """Continuous-batching serving on a finite seeded trace: Poisson arrivals at 20/s,
+    L log-uniform on {64..1024}, t_max = 10^U[3,5] MCS, 1-16 replicas, 12 log-spaced
+    measurements per request, 150 GB HBM budget, 16 slots."""
+    import torch
+
+    import __graft_entry__
+    from paper_2305_12161_gb300 import serve
+    __graft_entry__.build()
+    torch.cuda.init()
+    trace = serve.trace_requests(args.requests, seed=0, K=12)
+    offered = sum(r.L**3 * r.replicas * r.t_max for r in trace)
+    srv = serve.QuenchServer(budget_bytes=150e9, max_slots=16, quantum_mcs=64)
+    clocks = ClockSampler(0)
+    clocks.start()
+    res = srv.run(trace)
+    clk = clocks.stop()
+    summ = srv.summary()
+    arrivals = trace[-1].arrival_s
+    print(json.dumps({
+        "case": "serve", "metric": "time to result and aggregate spin updates/ns (serving)",
+        "requests": len(res), "p50_s": summ["p50_s"], "p99_s": summ["p99_s"], "makespan_s": summ["makespan_s"],
+        "aggregate_updates_per_ns": summ["updates_per_ns"], "updates": summ["updates"],
+        "offered_updates_per_s": offered / arrivals if arrivals > 0 else None,
+        "trace": "seeded Poisson 20/s, L log-uniform {64,...,1024}, t_max=10^U[3,5], replicas U{1..16}, K=12",
+        "slots": 16, "budget_gb": 150, "quantum_mcs": 64, "clocks": clk}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -222,19 +275,27 @@ def main():
     ap.add_argument("--L", type=int, default=2048)
     ap.add_argument("--mcs", type=int, default=1000)
     ap.add_argument("--t-checkpoint", type=int, default=10_000)
-    ap.add_argument("--K", type=int, default=8, help="measured times per leg")
+    ap.add_argument("--K", type=int, default=4, help="measured times per leg (4: one per decade)")
     ap.add_argument("--ref-L", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
-    ap.add_argument("--case", default="bench", choices=["bench", "quench"],
-                    help="quench: init + --mcs sweeps + one measurement, untimed (for profilers)")
+    ap.add_argument("--case", default="bench", choices=["bench", "quench", "serve", "batch"],
+                    help="quench: init + --mcs sweeps + one measurement, untimed (for profilers); "
+                         "serve: the serving loop on the first --requests arrivals of the seeded trace")
+    ap.add_argument("--requests", type=int, default=24)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
         return
     if args.case == "quench":
         run_quench_case(args)
+        return
+    if args.case == "serve":
+        run_serve_case(args)
+        return
+    if args.case == "batch":
+        run_batch_case(args)
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -314,7 +375,7 @@ def main():
                     q.measure_device(rec_dev[leg, k], der_dev[leg, k], c=0.5)
                 c = ev() if timing else None
                 if timing:
-                    sweep_events.append((a, b, 2 * (off - (offsets[k - 1] if k else 0))))
+                    sweep_events.append((a, b, 2 * (off - (offsets[k - 1] if k else 0)), leg))
                     meas_events.append((b, c))
         return outs
 
@@ -329,10 +390,7 @@ def main():
         end = ev()
         torch.cuda.synchronize()
         ms = start.elapsed_time(end)
-        if dist:
-            tt = torch.tensor([ms], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            ms = float(tt.item())
+        ms, _ = aggregate_ranks(ms, 0.0, dist, "cuda")
         return ms, q.launch_count() - l0
 
     for _ in range(args.warmup):
@@ -352,11 +410,14 @@ def main():
         batched = run_batched(torch, ising, inputs)
 
     updates_per_step = 2 * MCS * N
-    value = world * updates_per_step * args.steps / (ms * 1e-3) / 1e9
+    _, job_updates = aggregate_ranks(ms, float(updates_per_step * args.steps), dist, "cuda")
+    value = job_updates / (ms * 1e-3) / 1e9
 
     # per-kernel live timings (CUDA events on the launching stream, inside the timed region)
-    sweep_ms = sum(a.elapsed_time(b) for a, b, _ in sweep_events)
-    sweep_launches = sum(n for _, _, n in sweep_events)
+    sweep_ms = sum(a.elapsed_time(b) for a, b, _, _ in sweep_events)
+    sweep_launches = sum(n for _, _, n, _ in sweep_events)
+    leg_ms = [sum(a.elapsed_time(b) for a, b, _, lg in sweep_events if lg == g) for g in (0, 1)]
+    leg_launches = [sum(n for _, _, n, lg in sweep_events if lg == g) for g in (0, 1)]
     meas_ms = sum(a.elapsed_time(b) for a, b in meas_events)
     pk = _peaks()
     bytes_per_launch = 3 * (N // 2) / 8  # read q, read q-bar, write q: 1 bit each per site
@@ -368,7 +429,7 @@ def main():
     meas_avg_s = meas_ms * 1e-3 / n_meas
     popc_peak = 152 * 16 * pk["sm_max_mhz"] * 1e6 / 1e12  # T popc/s: 16 POPC lanes per SM per clock
     corr_tops = corr_ops / meas_avg_s / 1e12
-    roof_sweep = {"kernel": "k_sweep_zmarch (half-sweep)", "bound": "hbm", "achieved": sweep_gbs,
+    roof_sweep = {"kernel": "k_sweep_zfast (half-sweep)", "bound": "hbm", "achieved": sweep_gbs,
                   "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": sweep_gbs / pk["hbm_gbs"], "traffic": None,
                   "peak_src": pk["src"], "avg_launch_ms": sweep_avg_s * 1e3, "bytes_per_launch": bytes_per_launch,
                   "updates_per_ns": (N // 2) / sweep_avg_s / 1e9}
@@ -392,7 +453,11 @@ def main():
                        "l2": "inputs larger than L2 (1 GiB packed lattice > 129 MB)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roof, "roofline_sweep": roof_sweep, "roofline_measure": roof_corr,
-            "breakdown_ms_per_step": {"sweeps": sweep_ms / args.steps, "measurements": meas_ms / args.steps},
+            "breakdown_ms_per_step": {"sweeps": sweep_ms / args.steps, "measurements": meas_ms / args.steps,
+                                      "sweeps_leg_i_t0": leg_ms[0] / args.steps,
+                                      "sweeps_leg_ii_t1e4": leg_ms[1] / args.steps},
+            "sweep_updates_per_ns_by_leg": [(N // 2) * n / (ms_ * 1e-3) / 1e9 if ms_ > 0 else None
+                                            for n, ms_ in zip(leg_launches, leg_ms)],
             "sweep_only_updates_per_ns": world * (N // 2) / sweep_avg_s / 1e9,
             "clocks": clk, "e2e": e2e, "gpu_launches": launches, "batched": batched,
             "cpu_baseline": cpu,

@@ -72,10 +72,12 @@ typedef struct {
     int device;     /* CUDA device ordinal; -1: the current device */
     int variant;    /* packed sweep kernel variant, 0 = automatic (see ising_variants):
                        1 one thread per word (any L), 2 z-marching tiles (L multiple of 256),
-                       3 z-marching specialised on the row width (L = 256, 512, 1024, 2048) */
+                       3 z-marching specialised on the row width (L = 256, 512, 1024, 2048),
+                       4 as 3 with a deeper copy pipeline and fewer registers */
     int tile_y;     /* packed z-marching variant: rows per tile (0 = automatic); variant 3
                        (z-marching specialised on the row width) fixes it to 256/(L/256) */
     int tile_z;     /* packed z-marching variant: planes per tile (0 = automatic) */
+    int depth;      /* variant 4: planes in flight in the copy pipeline, 2..4 (0 = 3) */
 } ising_opts;
 
 /* Fill *opts with the defaults: GLAUBER, PACKED, own stream, current device, auto. */

@@ -98,6 +98,7 @@ void ising_default_opts(ising_opts *o)
     o->variant = 0;
     o->tile_y = 0;
     o->tile_z = 0;
+    o->depth = 0;
 }
 
 int64_t ising_record_len(int L)
@@ -132,10 +133,10 @@ int64_t ising_launch_count(const ising_ctx *c) { return c ? c->launches : -1; }
 
 int ising_variants(int *ids, int cap)
 {
-    const int all[3] = {VARIANT_WORD, VARIANT_ZMARCH, VARIANT_ZFAST};
-    if (!ids) return 3;
+    const int all[4] = {VARIANT_WORD, VARIANT_ZMARCH, VARIANT_ZFAST, VARIANT_ZDEEP};
+    if (!ids) return 4;
     int n = 0;
-    for (int i = 0; i < 3 && n < cap; ++i) ids[n++] = all[i];
+    for (int i = 0; i < 4 && n < cap; ++i) ids[n++] = all[i];
     return n;
 }
 
@@ -198,15 +199,17 @@ int ising_create_ex(ising_ctx **out, int L, int R, uint64_t seed, const ising_op
     if (o.variant == 0) {
         c->cfg = default_sweep_config(L, R);
     } else {
-        c->cfg = SweepConfig{o.variant, o.tile_y, o.tile_z};
-        if ((c->cfg.variant == VARIANT_ZMARCH || c->cfg.variant == VARIANT_ZFAST) && (o.tile_y == 0 || o.tile_z == 0)) {
+        c->cfg = SweepConfig{o.variant, o.tile_y, o.tile_z, o.depth ? o.depth : 3};
+        if ((c->cfg.variant == VARIANT_ZMARCH || c->cfg.variant == VARIANT_ZFAST || c->cfg.variant == VARIANT_ZDEEP) &&
+            (o.tile_y == 0 || o.tile_z == 0)) {
             if (L >= 256 && L % 256 == 0) {
                 const int W4 = L / 256;
                 if (!c->cfg.tile_y) c->cfg.tile_y = std::max(1, 256 / W4);
                 if (!c->cfg.tile_z) c->cfg.tile_z = std::min(L, 16);
             }
         }
-        if (c->cfg.variant == VARIANT_ZFAST && L >= 256 && L % 256 == 0) c->cfg.tile_y = 256 / (L / 256);
+        if ((c->cfg.variant == VARIANT_ZFAST || c->cfg.variant == VARIANT_ZDEEP) && L >= 256 && L % 256 == 0)
+            c->cfg.tile_y = 256 / (L / 256);
         if (!sweep_config_valid(L, c->cfg)) return bail(ISING_EINVAL);
     }
     // stream-ordered allocations (no implicit device synchronisation)
@@ -436,18 +439,22 @@ int ising_tune_sweep(int L, int replicas, int probe_mcs, const ising_opts *base,
     if (base) o = *base;
     if (o.form != ISING_FORM_PACKED) return ISING_EINVAL;
     std::vector<SweepConfig> cands;
-    cands.push_back(SweepConfig{VARIANT_WORD, 0, 0});
+    cands.push_back(SweepConfig{VARIANT_WORD, 0, 0, 0});
     const int tzs[] = {4, 8, 16, 32, 64};
     if (L >= 256 && L % 256 == 0) {
         const int W4 = L / 256;
         for (int ty = 1; ty <= L; ty *= 2)
             for (int tz : tzs) {
-                const SweepConfig c{VARIANT_ZMARCH, ty, tz};
+                const SweepConfig c{VARIANT_ZMARCH, ty, tz, 0};
                 if (ty * W4 >= 64 && sweep_config_valid(L, c)) cands.push_back(c);
             }
         for (int tz : tzs) {
-            const SweepConfig c{VARIANT_ZFAST, 256 / W4, tz};
+            const SweepConfig c{VARIANT_ZFAST, 256 / W4, tz, 0};
             if (sweep_config_valid(L, c)) cands.push_back(c);
+            for (int d = 2; d <= 4; ++d) {
+                const SweepConfig cd{VARIANT_ZDEEP, 256 / W4, tz, d};
+                if (sweep_config_valid(L, cd)) cands.push_back(cd);
+            }
         }
     }
     double best_ms = 1e300;
@@ -457,6 +464,7 @@ int ising_tune_sweep(int L, int replicas, int probe_mcs, const ising_opts *base,
         oc.variant = c.variant;
         oc.tile_y = c.tile_y;
         oc.tile_z = c.tile_z;
+        oc.depth = c.depth;
         ising_ctx *ctx = nullptr;
         int st = ising_create_ex(&ctx, L, replicas, 1, &oc);
         if (st != ISING_OK) continue;

@@ -83,8 +83,9 @@ __global__ void k_mb(const uint32_t *lat, Geom g, int64_t *rec)
 // RT consecutive lags r0..r0+RT-1): the item keeps a register window of the RT partner
 // words col[j + r0 .. j + r0 + RT - 1] and slides it along j, so each step costs one
 // broadcast load (col[j]) and one window load for RT XOR pairs.  The XOR words of each
-// lag are summed by carry-save adders (Harley & Seal's popcount accumulation), which
-// needs one POPC per eight words instead of one per word.
+// lag are summed either by POPC per word or by carry-save adders (Harley & Seal's
+// popcount accumulation, one POPC per eight words); warps are split between the two so
+// that the bit-count unit and the ALU are busy together.
 __host__ __device__ inline int corr_nc(int L)
 {
     int nc = 8192 / L;
@@ -193,7 +194,11 @@ __global__ void __launch_bounds__(NT) k_corr(const uint32_t *lat, Geom g, int64_
 #pragma unroll
             for (int k = 0; k < RT; ++k) win[k] = col[corr_pad(r0 + k)];
             unsigned int total[RT];
-            if (RT == 8) {
+            // Two ways to sum the XOR words, each saturating a different pipe: POPC per
+            // word (bound by the 16-lane/clk bit-count unit) or carry-save adders (bound by
+            // the ALU).  Warps 5..7 of every 8 take the carry-save path so that both pipes
+            // work at once; the choice is per warp, so no warp diverges.
+            if (RT == 8 && (wid & 7) >= 5) {
                 // Harley-Seal carry-save accumulation per lag: eight XOR words pass through
                 // seven carry-save adders into (ones, twos, fours) and one "eights" word,
                 // so one POPC covers eight words.

@@ -320,6 +320,126 @@ __global__ void __launch_bounds__(256) k_sweep_zfast(uint32_t *lat, Geom g, int 
 }
 
 // ---------------------------------------------------------------------------------
+// ZDEEP variant: the ZFAST tile walk with a deeper copy pipeline.  Both sublattices'
+// planes stream through shared-memory rings by cp.async, AHEAD planes beyond the one
+// being consumed (other ring AHEAD+3 slots, own ring AHEAD+1), and the Philox round keys
+// are recomputed per call instead of held in registers, so more CTAs fit per SM.  The
+// sweep is bound by memory latency (its speed does not change between dense-tie and
+// sparse-tie times), which both measures address: more bytes in flight per SM.
+template <int RULE, int W4, int AHEAD>
+__global__ void __launch_bounds__(256) k_sweep_zdeep(uint32_t *lat, Geom g, int q, uint32_t t, uint64_t seed, int TZ)
+{
+    constexpr int NT = 256, TY = NT / W4;
+    constexpr int OSZ = (TY + 2) * W4;
+    constexpr int NS = AHEAD + 3, NQ = AHEAD + 1;
+    extern __shared__ uint4 dsm[];
+    uint4 *ring = dsm;             // NS * OSZ
+    uint4 *qring = dsm + NS * OSZ; // NQ * NT
+    const int L = g.L;
+    const int tid = threadIdx.x;
+    const int ty = tid / W4, cx = tid % W4;
+    const int nty = L / TY;
+    const int y0 = (int)(blockIdx.x % nty) * TY;
+    const int z0 = (int)(blockIdx.x / nty) * TZ;
+    const int r = blockIdx.y;
+    uint4 *S4 = reinterpret_cast<uint4 *>(lat + (2 * (int64_t)r + q) * g.nw);
+    const uint4 *O4 = reinterpret_cast<const uint4 *>(lat + (2 * (int64_t)r + (1 - q)) * g.nw);
+    const uint64_t key = seed + (uint64_t)r;
+    const int64_t plane4 = (int64_t)L * W4;
+    int ya = y0 - 1 + ty;
+    ya = ya < 0 ? ya + L : ya;
+    const int64_t offa = (int64_t)ya * W4 + cx;
+    const bool halo = tid < 2 * W4;
+    int yb = y0 - 1 + TY + ty;
+    yb = yb >= L ? yb - L : yb;
+    const int64_t offb = (int64_t)yb * W4 + cx;
+    const int y = y0 + ty;
+    const int64_t own = (int64_t)y * W4 + cx;
+
+    // group gi: other plane z0-1+gi -> ring slot gi % NS; own plane z0+gi-2 (gi >= 2) ->
+    // qring slot gi % NQ.  Slots are tracked incrementally.
+    int so_issue = 0, sq_issue = 0;
+    auto issue = [&](int gi) {
+        if (gi <= TZ + 1) {
+            int pz = z0 - 1 + gi;
+            pz = pz < 0 ? pz + L : (pz >= L ? pz - L : pz);
+            const uint4 *src = O4 + (int64_t)pz * plane4;
+            uint4 *dst = ring + so_issue * OSZ;
+            cp_async16(dst + tid, src + offa);
+            if (halo) cp_async16(dst + NT + tid, src + offb);
+        }
+        if (gi >= 2 && gi <= TZ + 1) cp_async16(qring + sq_issue * NT + tid, S4 + (int64_t)(z0 + gi - 2) * plane4 + own);
+        cp_async_commit();
+        so_issue = so_issue == NS - 1 ? 0 : so_issue + 1;
+        sq_issue = sq_issue == NQ - 1 ? 0 : sq_issue + 1;
+    };
+
+#pragma unroll 1
+    for (int gi = 0; gi < AHEAD + 2; ++gi) issue(gi);
+    cp_async_wait<AHEAD>();  // groups 0 and 1 have landed
+    __syncthreads();
+    uint4 cm = ring[0 * OSZ + (ty + 1) * W4 + cx];
+    uint4 cc = ring[1 * OSZ + (ty + 1) * W4 + cx];
+    const int cxl = (cx + W4 - 1) % W4, cxr = (cx + 1) % W4;
+    int sz = 1;       // ring slot of other plane z  (group i+1)
+    int sqz = 2 % NQ; // qring slot of own plane z   (group i+2)
+#pragma unroll 1
+    for (int i = 0; i < TZ; ++i) {
+        cp_async_wait<AHEAD - 1>();  // group i+2 has landed
+        __syncthreads();
+        issue(i + 2 + AHEAD);        // overwrites other plane z-2 and own plane z-1 (both done)
+        const int z = z0 + i;
+        const int szp = sz == NS - 1 ? 0 : sz + 1;
+        const uint4 *Oz = ring + sz * OSZ;
+        const uint4 cp = ring[szp * OSZ + (ty + 1) * W4 + cx];
+        const uint4 ym = Oz[ty * W4 + cx];
+        const uint4 yp = Oz[(ty + 2) * W4 + cx];
+        const uint4 s = qring[sqz * NT + tid];
+        const int p = (y + z + q) & 1;
+        uint4 X;
+        if (p == 0) {
+            const uint32_t e = Oz[(ty + 1) * W4 + cxl].w;
+            X.x = __funnelshift_l(e, cc.x, 1);
+            X.y = __funnelshift_l(cc.x, cc.y, 1);
+            X.z = __funnelshift_l(cc.y, cc.z, 1);
+            X.w = __funnelshift_l(cc.z, cc.w, 1);
+        } else {
+            const uint32_t e = Oz[(ty + 1) * W4 + cxr].x;
+            X.x = __funnelshift_r(cc.x, cc.y, 1);
+            X.y = __funnelshift_r(cc.y, cc.z, 1);
+            X.z = __funnelshift_r(cc.z, cc.w, 1);
+            X.w = __funnelshift_r(cc.w, e, 1);
+        }
+        uint32_t g0, g1, g2, g3, e0, e1, e2, e3;
+        count6(cc.x, X.x, ym.x, yp.x, cm.x, cp.x, g0, e0);
+        count6(cc.y, X.y, ym.y, yp.y, cm.y, cp.y, g1, e1);
+        count6(cc.z, X.z, ym.z, yp.z, cm.z, cp.z, g2, e2);
+        count6(cc.w, X.w, ym.w, yp.w, cm.w, cp.w, g3, e3);
+        const uint32_t gidx = (uint32_t)((int64_t)z * plane4 + own);
+        U4 o{0u, 0u, 0u, 0u};
+        if (RULE == TIE_GLAUBER && (e0 | e1 | e2 | e3) != 0u)
+            o = philox4x32_10(gidx, t, (uint32_t)q, 0u, (uint32_t)key, (uint32_t)(key >> 32));
+        uint4 nw;
+        nw.x = resolve<RULE>(s.x, g0, e0, o.x);
+        nw.y = resolve<RULE>(s.y, g1, e1, o.y);
+        nw.z = resolve<RULE>(s.z, g2, e2, o.z);
+        nw.w = resolve<RULE>(s.w, g3, e3, o.w);
+        S4[(int64_t)z * plane4 + own] = nw;
+        cm = cc;
+        cc = cp;
+        sz = szp;
+        sqz = sqz == NQ - 1 ? 0 : sqz + 1;
+    }
+    cp_async_wait<0>();
+}
+
+static size_t zdeep_smem_bytes(int L, int ahead)
+{
+    const int W4 = L / 256, TY = 256 / W4;
+    return sizeof(uint4) * (size_t)((ahead + 3) * (TY + 2) * W4 + (ahead + 1) * 256);
+}
+
+// ---------------------------------------------------------------------------------
 static bool zfast_width_ok(int L) { return L % 256 == 0 && (L / 256 == 1 || L / 256 == 2 || L / 256 == 4 || L / 256 == 8); }
 
 bool sweep_config_valid(int L, const SweepConfig &c)
@@ -327,6 +447,9 @@ bool sweep_config_valid(int L, const SweepConfig &c)
     if (c.variant == VARIANT_WORD) return true;
     if (c.variant == VARIANT_ZFAST)
         return L >= 256 && zfast_width_ok(L) && c.tile_z >= 1 && L % c.tile_z == 0 && L % (256 / (L / 256)) == 0;
+    if (c.variant == VARIANT_ZDEEP)
+        return L >= 256 && zfast_width_ok(L) && c.tile_z >= 1 && L % c.tile_z == 0 && L % (256 / (L / 256)) == 0 &&
+               c.depth >= 2 && c.depth <= 4;
     if (c.variant != VARIANT_ZMARCH) return false;
     if (L < 256 || L % 256 != 0) return false;
     const int W4 = L / 256;
@@ -338,7 +461,7 @@ bool sweep_config_valid(int L, const SweepConfig &c)
 
 SweepConfig default_sweep_config(int L, int R)
 {
-    SweepConfig c{VARIANT_WORD, 0, 0};
+    SweepConfig c{VARIANT_WORD, 0, 0, 0};
     if (L >= 256 && L % 256 == 0) {
         const int W4 = L / 256;
         int ty = 256 / W4;
@@ -348,13 +471,13 @@ SweepConfig default_sweep_config(int L, int R)
         while (tz > 1 && L % tz != 0) tz >>= 1;
         // keep at least ~4 CTAs per SM-worth of tiles on small lattices
         while (tz > 4 && (int64_t)(L / ty) * (L / tz) * R < 4 * 152) tz >>= 1;
-        c = SweepConfig{VARIANT_ZMARCH, ty, tz};
-        if (!sweep_config_valid(L, c)) c = SweepConfig{VARIANT_WORD, 0, 0};
+        c = SweepConfig{VARIANT_ZMARCH, ty, tz, 0};
+        if (!sweep_config_valid(L, c)) c = SweepConfig{VARIANT_WORD, 0, 0, 0};
         if (zfast_width_ok(L)) {
             const int fty = 256 / W4;
             int ftz = 32;
             while (ftz > 4 && (int64_t)(L / fty) * (L / ftz) * R < 4 * 152) ftz >>= 1;
-            const SweepConfig f{VARIANT_ZFAST, fty, ftz};
+            const SweepConfig f{VARIANT_ZFAST, fty, ftz, 2};
             if (sweep_config_valid(L, f)) c = f;
         }
     }
@@ -366,7 +489,29 @@ static cudaError_t sweeps_rule(uint32_t *lat, int L, int R, uint64_t seed, int64
                                const SweepConfig &cfg, cudaStream_t s, int64_t *launches)
 {
     const Geom g = make_geom(L);
-    if (cfg.variant == VARIANT_ZFAST) {
+    if (cfg.variant == VARIANT_ZDEEP) {
+        const int W4 = L / 256;
+        const dim3 grid((unsigned)((L / (256 / W4)) * (L / cfg.tile_z)), (unsigned)R);
+        const size_t smem = zdeep_smem_bytes(L, cfg.depth);
+        void *fn = nullptr;
+#define ZD_CASE(w, a) \
+    if (W4 == w && cfg.depth == a) fn = (void *)k_sweep_zdeep<RULE, w, a>;
+        ZD_CASE(1, 2) ZD_CASE(1, 3) ZD_CASE(1, 4) ZD_CASE(2, 2) ZD_CASE(2, 3) ZD_CASE(2, 4)
+        ZD_CASE(4, 2) ZD_CASE(4, 3) ZD_CASE(4, 4) ZD_CASE(8, 2) ZD_CASE(8, 3) ZD_CASE(8, 4)
+#undef ZD_CASE
+        if (!fn) return cudaErrorInvalidValue;
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        for (int64_t k = 0; k < n; ++k) {
+            uint32_t t = (uint32_t)(t0 + k);
+            for (int q = 0; q < 2; ++q) {
+                int tz = cfg.tile_z;
+                void *args[] = {(void *)&lat, (void *)&g, (void *)&q, (void *)&t, (void *)&seed, (void *)&tz};
+                e = cudaLaunchKernel(fn, grid, dim3(256), args, smem, s);
+                if (e != cudaSuccess) return e;
+            }
+        }
+    } else if (cfg.variant == VARIANT_ZFAST) {
         const int W4 = L / 256;
         const dim3 grid((unsigned)((L / (256 / W4)) * (L / cfg.tile_z)), (unsigned)R);
         for (int64_t k = 0; k < n; ++k) {

@@ -17,12 +17,14 @@ enum SweepVariant : int {
     VARIANT_WORD = 1,    // one thread per 32-bit word, any supported L
     VARIANT_ZMARCH = 2,  // z-marching, cp.async-staged tiles, 128 spins per thread, L >= 256
     VARIANT_ZFAST = 3,   // z-marching specialised on the row width (L = 256, 512, 1024, 2048)
+    VARIANT_ZDEEP = 4,   // as ZFAST with a deeper copy pipeline (depth 2..4) and fewer registers
 };
 
 struct SweepConfig {
     int variant;
     int tile_y;  // rows per tile (z-march; ZFAST: fixed to 256 / (L/256))
     int tile_z;  // planes per tile (z-march)
+    int depth;   // ZDEEP: planes in flight beyond the one consumed (2..4)
 };
 
 bool sweep_config_valid(int L, const SweepConfig &c);

@@ -26,7 +26,7 @@ TIE_GLAUBER, TIE_ALWAYS, TIE_NEVER = 0, 1, 2
 FORM_PACKED, FORM_PLAIN = 0, 1
 MEAS_DEVICE, MEAS_CONNECTED, MEAS_NO_CORR = 1, 2, 4
 PTR_DEVICE = 1
-VARIANT_AUTO, VARIANT_WORD, VARIANT_ZMARCH, VARIANT_ZFAST = 0, 1, 2, 3
+VARIANT_AUTO, VARIANT_WORD, VARIANT_ZMARCH, VARIANT_ZFAST, VARIANT_ZDEEP = 0, 1, 2, 3, 4
 
 
 class IsingError(RuntimeError):
@@ -41,7 +41,7 @@ class IsingError(RuntimeError):
 class ising_opts(ctypes.Structure):
     _fields_ = [("tie", ctypes.c_int), ("form", ctypes.c_int), ("stream", ctypes.c_void_p),
                 ("device", ctypes.c_int), ("variant", ctypes.c_int), ("tile_y", ctypes.c_int),
-                ("tile_z", ctypes.c_int)]
+                ("tile_z", ctypes.c_int), ("depth", ctypes.c_int)]
 
 
 def lib_path() -> str:
@@ -157,11 +157,11 @@ class Ising:
     """One context: ``replicas`` lattices of size ``L`` (replica r seeded ``seed + r``)."""
 
     def __init__(self, L: int, replicas: int = 1, seed: int = 1, tie: int = TIE_GLAUBER, form: int = FORM_PACKED,
-                 stream=None, device: int = -1, variant: int = 0, tile_y: int = 0, tile_z: int = 0):
+                 stream=None, device: int = -1, variant: int = 0, tile_y: int = 0, tile_z: int = 0, depth: int = 0):
         self._h = ctypes.c_void_p()
         o = ising_opts()
         lib().ising_default_opts(ctypes.byref(o))
-        o.tie, o.form, o.device, o.variant, o.tile_y, o.tile_z = tie, form, device, variant, tile_y, tile_z
+        o.tie, o.form, o.device, o.variant, o.tile_y, o.tile_z, o.depth = tie, form, device, variant, tile_y, tile_z, depth
         sh = _stream_handle(stream)
         o.stream = sh if sh else None
         self._stream_obj = stream  # keep the caller's stream alive
@@ -286,7 +286,8 @@ def ising_tune_sweep(L: int, replicas: int = 1, probe_mcs: int = 8, tie: int = T
     st = lib().ising_tune_sweep(L, replicas, probe_mcs, ctypes.byref(base), ctypes.byref(best), ctypes.byref(ms))
     if st != ISING_OK:
         raise IsingError(st, "ising_tune_sweep")
-    return {"variant": best.variant, "tile_y": best.tile_y, "tile_z": best.tile_z, "ms_per_mcs": ms.value}
+    return {"variant": best.variant, "tile_y": best.tile_y, "tile_z": best.tile_z, "depth": best.depth,
+            "ms_per_mcs": ms.value}
 
 
 class Batch:

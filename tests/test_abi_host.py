@@ -44,7 +44,8 @@ def test_strerror_and_variants(lib):
     from paper_2305_12161_gb300 import ising
     for code in range(0, -7, -1):
         assert isinstance(ising.ising_strerror(code), str) and ising.ising_strerror(code)
-    assert ising.ising_variants() == [ising.VARIANT_WORD, ising.VARIANT_ZMARCH, ising.VARIANT_ZFAST]
+    assert ising.ising_variants() == [ising.VARIANT_WORD, ising.VARIANT_ZMARCH, ising.VARIANT_ZFAST,
+                                     ising.VARIANT_ZDEEP]
 
 
 def test_create_rejects_bad_arguments_before_touching_a_device(lib):

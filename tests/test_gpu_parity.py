@@ -83,6 +83,12 @@ def test_zfast_L256_vs_oracle(ising, tz):
     _compare(ising, 256, 1, 13, [1, 2, 5], variant=ising.VARIANT_ZFAST, tile_z=tz)
 
 
+@pytest.mark.parametrize("depth", [2, 3, 4])
+def test_zdeep_L256_vs_oracle(ising, depth):
+    _compare(ising, 256, 1, 14, [1, 2, 5], variant=ising.VARIANT_ZDEEP, tile_z=4, depth=depth)
+    _compare(ising, 256, 2, 15, [2], rule=1, variant=ising.VARIANT_ZDEEP, tile_z=1, depth=depth)
+
+
 def test_zfast_rules_and_replicas_L256(ising):
     for rule in (1, 2):
         _compare(ising, 256, 1, 6, [1, 3], rule=rule, variant=ising.VARIANT_ZFAST)
@@ -118,6 +124,10 @@ def test_variants_and_tiles_bit_identical(ising, L):
         got, grec = _packed_state(ising, L, 1, 9, 6, variant=ising.VARIANT_ZFAST, tile_z=tz)
         assert np.array_equal(got[0], ref[0]), ("zfast", tz)
         assert np.array_equal(grec, rec)
+        for d in (2, 3, 4):
+            got, grec = _packed_state(ising, L, 1, 9, 6, variant=ising.VARIANT_ZDEEP, tile_z=tz, depth=d)
+            assert np.array_equal(got[0], ref[0]), ("zdeep", tz, d)
+            assert np.array_equal(grec, rec)
 
 
 def test_plain_and_packed_forms_identical_L256(ising):
