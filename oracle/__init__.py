@@ -79,6 +79,17 @@ def lib() -> ctypes.CDLL:
             L.orc_magnetisation_bonds.restype = None
             L.orc_corr_lag.argtypes = [ctypes.c_int, i8p, ctypes.c_int64, i64p]
             L.orc_corr_lag.restype = None
+            L.orc_menger_member.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int]
+            L.orc_menger_member.restype = ctypes.c_int
+            L.orc_menger_tile_sign.argtypes = [ctypes.c_uint64, ctypes.c_int64]
+            L.orc_menger_tile_sign.restype = ctypes.c_int
+            L.orc_init_menger.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_int, i8p]
+            L.orc_init_menger.restype = None
+            L.orc_mixed_order.argtypes = [ctypes.c_uint64, ctypes.c_uint32]
+            L.orc_mixed_order.restype = ctypes.c_int
+            L.orc_sweeps_mixed.argtypes = [ctypes.c_int, i8p, ctypes.c_uint32, ctypes.c_int64,
+                                           ctypes.c_uint64, ctypes.c_int]
+            L.orc_sweeps_mixed.restype = None
             L.orc_derived.argtypes = [ctypes.c_int, i64p, ctypes.c_double, ctypes.c_int, f64p]
             L.orc_derived.restype = None
             _lib = L
@@ -136,6 +147,31 @@ def sweeps(s: np.ndarray, t0: int, n: int, S: int, rule: int = TIE_GLAUBER) -> N
     """``n`` MCS in place, starting at completed-sweep count ``t0``."""
     L = _check_lattice(s)
     lib().orc_sweeps(L, _p(s, ctypes.c_int8), t0, n, S % 2**64, rule)
+
+
+def menger_member(a: int, b: int, c: int, k: int) -> bool:
+    return bool(lib().orc_menger_member(a, b, c, k))
+
+
+def menger_tile_sign(S: int, T: int) -> int:
+    return int(lib().orc_menger_tile_sign(S % 2**64, T))
+
+
+def init_menger(L: int, seed: int, k: int, replica: int = 0) -> np.ndarray:
+    """Menger-sponge start of iteration k (tiles of side 3^k, random sign per tile)."""
+    s = np.empty((L, L, L), dtype=np.int8)
+    lib().orc_init_menger(L, (seed + replica) % 2**64, k, _p(s, ctypes.c_int8))
+    return s
+
+
+def mixed_order(S: int, t: int) -> int:
+    """1 when sweep t of the mixed cycle updates blue (q = 1) first."""
+    return int(lib().orc_mixed_order(S % 2**64, t))
+
+
+def sweeps_mixed(s: np.ndarray, t0: int, n: int, S: int, rule: int = TIE_GLAUBER) -> None:
+    L = _check_lattice(s)
+    lib().orc_sweeps_mixed(L, _p(s, ctypes.c_int8), t0, n, S % 2**64, rule)
 
 
 def record_len(L: int) -> int:

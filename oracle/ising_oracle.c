@@ -311,3 +311,73 @@ void orc_derived(int L_, const int64_t *rec, double c, int connected, double *ou
     }
     out[3] = lc;
 }
+
+/* ------------------------------------------------------------------------------ */
+/* Menger-sponge initial state (Results, the sponge test: the lattice is tiled with
+ * k-th-iteration Menger sponges of side 3^k, each drawn in up or down spins at random).
+ * Reading used here: a cell (a,b,c) of a tile, 0 <= a,b,c < 3^k, belongs to the sponge
+ * unless at some base-3 digit position at least two of its three digits equal 1 (the
+ * centre and face-centre sub-cubes removed at every level); the sponge's cells take the
+ * tile's sign sigma, the removed cells take -sigma.  Tiles are cut at the lattice edge when
+ * 3^k does not divide L.  Tile T = tx + nT*(ty + nT*tz), nT = ceil(L/3^k), gets sigma = +1
+ * when bit (T & 31) of word ((T >> 5) & 3) of Philox(counter (T >> 7, 0, 4, 0), key S) is 1. */
+int orc_menger_member(int64_t a, int64_t b, int64_t c, int k)
+{
+    for (int d = 0; d < k; ++d) {
+        int ones = (a % 3 == 1) + (b % 3 == 1) + (c % 3 == 1);
+        if (ones >= 2) return 0;
+        a /= 3;
+        b /= 3;
+        c /= 3;
+    }
+    return 1;
+}
+
+int orc_menger_tile_sign(uint64_t S, int64_t T)
+{
+    uint32_t ctr[4] = {(uint32_t)(T >> 7), 0u, 4u, 0u};
+    uint32_t key[2] = {(uint32_t)(S & 0xffffffffu), (uint32_t)(S >> 32)};
+    uint32_t o[4];
+    orc_philox4x32_10(ctr, key, o);
+    return ((o[(T >> 5) & 3] >> (T & 31)) & 1u) ? 1 : -1;
+}
+
+void orc_init_menger(int L_, uint64_t S, int k, int8_t *s)
+{
+    const int64_t L = L_;
+    int64_t side = 1;
+    for (int d = 0; d < k; ++d) side *= 3;
+    const int64_t nT = (L + side - 1) / side;
+#pragma omp parallel for schedule(static)
+    for (int64_t z = 0; z < L; ++z)
+        for (int64_t y = 0; y < L; ++y)
+            for (int64_t x = 0; x < L; ++x) {
+                int64_t T = x / side + nT * (y / side + nT * (z / side));
+                int sigma = orc_menger_tile_sign(S, T);
+                int in = orc_menger_member(x % side, y % side, z % side, k);
+                s[site(L, x, y, z)] = (int8_t)(in ? sigma : -sigma);
+            }
+}
+
+/* ------------------------------------------------------------------------------ */
+/* Mixed cycle (Supp. Methods I B: the sublattice updated first is chosen at random in
+ * every sweep, which restores detailed balance).  Sweep t updates blue (q = 1) first when
+ * bit 0 of word 0 of Philox(counter (0, t, 5, 0), key S) is 1, otherwise red first. */
+int orc_mixed_order(uint64_t S, uint32_t t)
+{
+    uint32_t ctr[4] = {0u, t, 5u, 0u};
+    uint32_t key[2] = {(uint32_t)(S & 0xffffffffu), (uint32_t)(S >> 32)};
+    uint32_t o[4];
+    orc_philox4x32_10(ctr, key, o);
+    return (int)(o[0] & 1u);
+}
+
+void orc_sweeps_mixed(int L, int8_t *s, uint32_t t0, int64_t n, uint64_t S, int rule)
+{
+    for (int64_t k = 0; k < n; ++k) {
+        uint32_t t = t0 + (uint32_t)k;
+        int first = orc_mixed_order(S, t);
+        orc_half_sweep(L, s, first, t, S, rule, NULL, NULL);
+        orc_half_sweep(L, s, 1 - first, t, S, rule, NULL, NULL);
+    }
+}
