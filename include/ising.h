@@ -78,7 +78,16 @@ typedef struct {
                        (z-marching specialised on the row width) fixes it to 256/(L/256) */
     int tile_z;     /* packed z-marching variant: planes per tile (0 = automatic) */
     int depth;      /* variant 4: planes in flight in the copy pipeline, 2..4 (0 = 3) */
+    int cycle;      /* ising_cycle: sublattice order of each sweep */
 } ising_opts;
+
+/* Sublattice order of a sweep.  01: red (q = 0) then blue every sweep (the paper's main
+ * runs, Methods).  MIXED: the first sublattice of each sweep is random (Supp. Methods I B,
+ * the "mixed cycle" that restores detailed balance): sweep t of the lattice keyed S goes
+ * blue first when bit 0 of word 0 of Philox(counter (0, t, 5, 0), key S) is 1.  With
+ * replicas > 1 each replica draws its own order (one launch per replica and half-sweep).
+ * The batched form supports the 01 cycle only. */
+typedef enum { ISING_CYCLE_01 = 0, ISING_CYCLE_MIXED = 1 } ising_cycle;
 
 /* Fill *opts with the defaults: GLAUBER, PACKED, own stream, current device, auto. */
 void ising_default_opts(ising_opts *opts);
@@ -94,6 +103,15 @@ int ising_create_ex(ising_ctx **out, int L, int replicas, uint64_t seed, const i
 /* Redraw every replica's T = infinity initial state for a new seed (replica r uses
  * seed + r) and reset t to 0, reusing the context's memory.  Enqueued, no sync. */
 int ising_reinit(ising_ctx *ctx, uint64_t seed);
+
+/* Replace every replica's state by a Menger-sponge start (Results, the sponge test):
+ * tiles of k-th-iteration sponges of side 3^k (cut at the lattice edge), a cell in the
+ * sponge unless at some base-3 digit position two or three of its coordinates' digits
+ * are 1; sponge cells take the tile's random sign, removed cells the opposite.  Tile
+ * T = tx + nT*(ty + nT*tz), nT = ceil(L/3^k), is +1 when bit (T & 31) of word
+ * ((T >> 5) & 3) of Philox(counter (T >> 7, 0, 4, 0), key seed + replica) is 1.
+ * k = 0..8; resets t to 0.  Enqueued, no sync. */
+int ising_init_menger(ising_ctx *ctx, int k);
 
 /* Enqueue n_mcs >= 0 Monte Carlo sweeps on every replica (each sweep: red half-sweep,
  * then blue half-sweep; Methods, "Checkerboard update").  Advances the context's

@@ -44,8 +44,8 @@ struct U4 {
     uint32_t x, y, z, w;
 };
 
-__device__ __forceinline__ U4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
-                                            uint32_t k0, uint32_t k1)
+__host__ __device__ __forceinline__ U4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                                     uint32_t k0, uint32_t k1)
 {
     const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
     const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
@@ -102,7 +102,7 @@ __device__ __forceinline__ U4 philox4x32_10_rk(uint32_t c0, uint32_t c1, uint32_
     return U4{c0, c1, c2, c3};
 }
 
-__device__ __forceinline__ uint32_t pick(const U4 &o, int i)
+__host__ __device__ __forceinline__ uint32_t pick(const U4 &o, int i)
 {
     return i == 0 ? o.x : (i == 1 ? o.y : (i == 2 ? o.z : o.w));
 }

@@ -99,6 +99,7 @@ void ising_default_opts(ising_opts *o)
     o->tile_y = 0;
     o->tile_z = 0;
     o->depth = 0;
+    o->cycle = 0;
 }
 
 int64_t ising_record_len(int L)
@@ -168,6 +169,7 @@ int ising_create_ex(ising_ctx **out, int L, int R, uint64_t seed, const ising_op
     if (opts) o = *opts;
     if (L < 4 || L % 2 != 0 || R < 1 || R > 65535) return ISING_EINVAL;
     if (o.tie < 0 || o.tie > 2 || (o.form != ISING_FORM_PACKED && o.form != ISING_FORM_PLAIN)) return ISING_EINVAL;
+    if (o.cycle != ISING_CYCLE_01 && o.cycle != ISING_CYCLE_MIXED) return ISING_EINVAL;
     // the measurement kernels always run on the packed store
     if (!packed_L_ok(L)) return ISING_EINVAL;
     if ((int64_t)L > 4096) return ISING_EINVAL;  // 32-bit Philox group index bound
@@ -259,6 +261,23 @@ int ising_reinit(ising_ctx *c, uint64_t seed)
     return ISING_OK;
 }
 
+int ising_init_menger(ising_ctx *c, int k)
+{
+    int s = check_ctx(c);
+    if (s) return s;
+    if (k < 0 || k > 8) return fail(c, ISING_EINVAL, "Menger iteration must be in 0..8");
+    DeviceGuard dg(c->device);
+    if (c->L < 64) CK(c, cudaMemsetAsync(c->lat, 0, lattice_bytes_packed(c->L, c->R), c->stream));
+    CK(c, launch_init_menger(c->lat, c->L, c->R, c->seed, k, c->stream));
+    c->launches += 1;
+    if (c->opts.form == ISING_FORM_PLAIN) {
+        CK(c, launch_unpack(c->lat, c->plain, c->L, c->R, c->stream));
+        c->launches += 1;
+    }
+    c->t = 0;
+    return ISING_OK;
+}
+
 int ising_sweep(ising_ctx *c, int64_t n)
 {
     int s = check_ctx(c);
@@ -269,9 +288,11 @@ int ising_sweep(ising_ctx *c, int64_t n)
     DeviceGuard dg(c->device);
     cudaError_t e;
     if (c->opts.form == ISING_FORM_PLAIN)
-        e = launch_sweeps_plain(c->plain, c->L, c->R, c->seed, c->opts.tie, c->t, n, c->stream, &c->launches);
+        e = launch_sweeps_plain(c->plain, c->L, c->R, c->seed, c->opts.tie, c->t, n, c->opts.cycle, c->stream,
+                                &c->launches);
     else
-        e = launch_sweeps_packed(c->lat, c->L, c->R, c->seed, c->opts.tie, c->t, n, c->cfg, c->stream, &c->launches);
+        e = launch_sweeps_packed(c->lat, c->L, c->R, c->seed, c->opts.tie, c->t, n, c->opts.cycle, c->cfg, c->stream,
+                                 &c->launches);
     if (e != cudaSuccess) return cuda_fail(c, e, "sweep launch");
     c->t += n;
     return ISING_OK;

@@ -484,9 +484,11 @@ SweepConfig default_sweep_config(int L, int R)
     return c;
 }
 
+// One half-sweep of sublattice q at sweep t for R replicas starting at `lat` (replica r
+// keyed seed + r), with the configured kernel variant.
 template <int RULE>
-static cudaError_t sweeps_rule(uint32_t *lat, int L, int R, uint64_t seed, int64_t t0, int64_t n,
-                               const SweepConfig &cfg, cudaStream_t s, int64_t *launches)
+static cudaError_t half_sweep_rule(uint32_t *lat, int L, int R, uint64_t seed, int q, uint32_t t,
+                                   const SweepConfig &cfg, cudaStream_t s)
 {
     const Geom g = make_geom(L);
     if (cfg.variant == VARIANT_ZDEEP) {
@@ -502,67 +504,141 @@ static cudaError_t sweeps_rule(uint32_t *lat, int L, int R, uint64_t seed, int64
         if (!fn) return cudaErrorInvalidValue;
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        for (int64_t k = 0; k < n; ++k) {
-            uint32_t t = (uint32_t)(t0 + k);
-            for (int q = 0; q < 2; ++q) {
-                int tz = cfg.tile_z;
-                void *args[] = {(void *)&lat, (void *)&g, (void *)&q, (void *)&t, (void *)&seed, (void *)&tz};
-                e = cudaLaunchKernel(fn, grid, dim3(256), args, smem, s);
-                if (e != cudaSuccess) return e;
-            }
-        }
-    } else if (cfg.variant == VARIANT_ZFAST) {
+        int tz = cfg.tile_z;
+        void *args[] = {(void *)&lat, (void *)&g, (void *)&q, (void *)&t, (void *)&seed, (void *)&tz};
+        return cudaLaunchKernel(fn, grid, dim3(256), args, smem, s);
+    }
+    if (cfg.variant == VARIANT_ZFAST) {
         const int W4 = L / 256;
         const dim3 grid((unsigned)((L / (256 / W4)) * (L / cfg.tile_z)), (unsigned)R);
-        for (int64_t k = 0; k < n; ++k) {
-            const uint32_t t = (uint32_t)(t0 + k);
-            for (int q = 0; q < 2; ++q) {
-                switch (W4) {
-                case 1: k_sweep_zfast<RULE, 1><<<grid, 256, 0, s>>>(lat, g, q, t, seed, cfg.tile_z); break;
-                case 2: k_sweep_zfast<RULE, 2><<<grid, 256, 0, s>>>(lat, g, q, t, seed, cfg.tile_z); break;
-                case 4: k_sweep_zfast<RULE, 4><<<grid, 256, 0, s>>>(lat, g, q, t, seed, cfg.tile_z); break;
-                default: k_sweep_zfast<RULE, 8><<<grid, 256, 0, s>>>(lat, g, q, t, seed, cfg.tile_z); break;
-                }
-            }
+        switch (W4) {
+        case 1: k_sweep_zfast<RULE, 1><<<grid, 256, 0, s>>>(lat, g, q, t, seed, cfg.tile_z); break;
+        case 2: k_sweep_zfast<RULE, 2><<<grid, 256, 0, s>>>(lat, g, q, t, seed, cfg.tile_z); break;
+        case 4: k_sweep_zfast<RULE, 4><<<grid, 256, 0, s>>>(lat, g, q, t, seed, cfg.tile_z); break;
+        default: k_sweep_zfast<RULE, 8><<<grid, 256, 0, s>>>(lat, g, q, t, seed, cfg.tile_z); break;
         }
-    } else if (cfg.variant == VARIANT_ZMARCH) {
+        return cudaGetLastError();
+    }
+    if (cfg.variant == VARIANT_ZMARCH) {
         const int W4 = L / 256;
         const size_t smem = zmarch_smem_bytes(L, cfg.tile_y);
-        static bool attr_set = false;  // idempotent; benign if repeated
-        if (!attr_set) {
-            cudaError_t e = cudaFuncSetAttribute(k_sweep_zmarch<RULE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 200 * 1024);
-            if (e != cudaSuccess) return e;
-            attr_set = true;
-        }
+        cudaError_t e =
+            cudaFuncSetAttribute(k_sweep_zmarch<RULE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (e != cudaSuccess) return e;
         const dim3 grid((unsigned)((L / cfg.tile_y) * (L / cfg.tile_z)), (unsigned)R);
-        const int block = cfg.tile_y * W4;
-        for (int64_t k = 0; k < n; ++k) {
-            const uint32_t t = (uint32_t)(t0 + k);
-            k_sweep_zmarch<RULE><<<grid, block, smem, s>>>(lat, g, 0, t, seed, cfg.tile_y, cfg.tile_z);
-            k_sweep_zmarch<RULE><<<grid, block, smem, s>>>(lat, g, 1, t, seed, cfg.tile_y, cfg.tile_z);
-        }
-    } else {
-        const dim3 grid((unsigned)grid_for(g.nw, 256, 8 * 152 * 4), (unsigned)R);
-        for (int64_t k = 0; k < n; ++k) {
-            const uint32_t t = (uint32_t)(t0 + k);
-            k_sweep_word<RULE><<<grid, 256, 0, s>>>(lat, g, 0, t, seed);
-            k_sweep_word<RULE><<<grid, 256, 0, s>>>(lat, g, 1, t, seed);
+        k_sweep_zmarch<RULE><<<grid, cfg.tile_y * W4, smem, s>>>(lat, g, q, t, seed, cfg.tile_y, cfg.tile_z);
+        return cudaGetLastError();
+    }
+    const dim3 grid((unsigned)grid_for(g.nw, 256, 8 * 152 * 4), (unsigned)R);
+    k_sweep_word<RULE><<<grid, 256, 0, s>>>(lat, g, q, t, seed);
+    return cudaGetLastError();
+}
+
+// Mixed cycle (Supp. Methods I B): sweep t of the lattice keyed S updates blue first when
+// bit 0 of word 0 of Philox(counter (0, t, 5, 0), key S) is 1.
+int mixed_first(uint64_t S, uint32_t t)
+{
+    const U4 o = philox4x32_10(0u, t, 5u, 0u, (uint32_t)S, (uint32_t)(S >> 32));
+    return (int)(o.x & 1u);
+}
+
+template <int RULE>
+static cudaError_t sweeps_rule(uint32_t *lat, int L, int R, uint64_t seed, int64_t t0, int64_t n, int cycle,
+                               const SweepConfig &cfg, cudaStream_t s, int64_t *launches)
+{
+    const int64_t nw2 = 2 * make_geom(L).nw;
+    for (int64_t k = 0; k < n; ++k) {
+        const uint32_t t = (uint32_t)(t0 + k);
+        if (cycle == 0) {  // 01 cycle: red, then blue, all replicas in one launch each
+            for (int q = 0; q < 2; ++q) {
+                cudaError_t e = half_sweep_rule<RULE>(lat, L, R, seed, q, t, cfg, s);
+                if (e != cudaSuccess) return e;
+            }
+            if (launches) *launches += 2;
+        } else {           // mixed cycle: each replica its own order
+            for (int r = 0; r < R; ++r) {
+                const uint64_t S = seed + (uint64_t)r;
+                const int first = mixed_first(S, t);
+                for (int h = 0; h < 2; ++h) {
+                    cudaError_t e = half_sweep_rule<RULE>(lat + (int64_t)r * nw2, L, 1, S, first ^ h, t, cfg, s);
+                    if (e != cudaSuccess) return e;
+                }
+            }
+            if (launches) *launches += 2 * R;
         }
     }
-    if (launches) *launches += 2 * n;
     return cudaGetLastError();
 }
 
 cudaError_t launch_sweeps_packed(uint32_t *lat, int L, int R, uint64_t seed, int rule, int64_t t0, int64_t n,
-                                 const SweepConfig &cfg, cudaStream_t s, int64_t *launches)
+                                 int cycle, const SweepConfig &cfg, cudaStream_t s, int64_t *launches)
 {
     if (n <= 0) return cudaSuccess;
     switch (rule) {
-    case TIE_GLAUBER: return sweeps_rule<TIE_GLAUBER>(lat, L, R, seed, t0, n, cfg, s, launches);
-    case TIE_ALWAYS: return sweeps_rule<TIE_ALWAYS>(lat, L, R, seed, t0, n, cfg, s, launches);
-    default: return sweeps_rule<TIE_NEVER>(lat, L, R, seed, t0, n, cfg, s, launches);
+    case TIE_GLAUBER: return sweeps_rule<TIE_GLAUBER>(lat, L, R, seed, t0, n, cycle, cfg, s, launches);
+    case TIE_ALWAYS: return sweeps_rule<TIE_ALWAYS>(lat, L, R, seed, t0, n, cycle, cfg, s, launches);
+    default: return sweeps_rule<TIE_NEVER>(lat, L, R, seed, t0, n, cycle, cfg, s, launches);
     }
+}
+
+// ---------------------------------------------------------------------------------
+// Menger-sponge start (Results, the sponge test): the lattice is tiled with sponges of
+// iteration k and side 3^k (tiles cut at the lattice edge).  A cell belongs to the sponge
+// unless at some base-3 digit position at least two of its coordinates' digits are 1;
+// sponge cells take the tile's random sign, the removed cells the opposite one.  Tile
+// T = tx + nT*(ty + nT*tz) has sign +1 when bit (T & 31) of word ((T >> 5) & 3) of
+// Philox(counter (T >> 7, 0, 4, 0), key S) is set.
+__device__ __forceinline__ bool menger_member(int a, int b, int c, int k)
+{
+    for (int d = 0; d < k; ++d) {
+        const int ones = (a % 3 == 1) + (b % 3 == 1) + (c % 3 == 1);
+        if (ones >= 2) return false;
+        a /= 3;
+        b /= 3;
+        c /= 3;
+    }
+    return true;
+}
+
+__global__ void k_init_menger(uint32_t *lat, Geom g, uint64_t seed, int k, int side, int nT)
+{
+    const int r = blockIdx.y, q = blockIdx.z;
+    uint32_t *Sq = lat + (2 * (int64_t)r + q) * g.nw;
+    const uint64_t S = seed + (uint64_t)r;
+    const int L = g.L;
+    for (int64_t sw = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; sw < g.nw;
+         sw += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = sw / g.W;
+        const int kw = (int)(sw - row * g.W);
+        const int y = (int)(row % L), z = (int)(row / L);
+        const int p = (y + z + q) & 1;
+        uint32_t word = 0u;
+        int64_t Tc = -1;
+        int sigma = 1;
+        for (int b = 0; b < g.RB; ++b) {
+            const int x = 2 * (32 * kw + b) + p;
+            const int64_t T = x / side + (int64_t)nT * (y / side + (int64_t)nT * (z / side));
+            if (T != Tc) {
+                const U4 o = philox4x32_10((uint32_t)(T >> 7), 0u, 4u, 0u, (uint32_t)S, (uint32_t)(S >> 32));
+                sigma = ((pick(o, (int)((T >> 5) & 3)) >> (T & 31)) & 1u) ? 1 : -1;
+                Tc = T;
+            }
+            const bool in = menger_member(x % side, y % side, z % side, k);
+            if ((in ? sigma : -sigma) > 0) word |= 1u << b;
+        }
+        Sq[sw] = word;
+    }
+}
+
+cudaError_t launch_init_menger(uint32_t *lat, int L, int R, uint64_t seed, int k, cudaStream_t s)
+{
+    const Geom g = make_geom(L);
+    int side = 1;
+    for (int d = 0; d < k; ++d) side *= 3;
+    const int nT = (L + side - 1) / side;
+    dim3 grid(grid_for(g.nw, 256, 65535), R, 2);
+    k_init_menger<<<grid, 256, 0, s>>>(lat, g, seed, k, side, nT);
+    return cudaGetLastError();
 }
 
 }  // namespace ising

@@ -100,7 +100,7 @@ cudaError_t launch_init_plain(int8_t *plain, int L, int R, uint64_t seed, cudaSt
 }
 
 template <int RULE>
-static void sweeps_plain_rule(int8_t *plain, const Geom &g, int R, uint64_t seed, int64_t t0, int64_t n,
+static void sweeps_plain_rule(int8_t *plain, const Geom &g, int R, uint64_t seed, int64_t t0, int64_t n, int cycle,
                               cudaStream_t s, int64_t *launches)
 {
     const int64_t N = (int64_t)g.L * g.L * g.L;
@@ -108,23 +108,25 @@ static void sweeps_plain_rule(int8_t *plain, const Geom &g, int R, uint64_t seed
     if (blocks > 152 * 64) blocks = 152 * 64;
     for (int64_t k = 0; k < n; ++k) {
         const uint32_t t = (uint32_t)(t0 + k);
-        for (int q = 0; q < 2; ++q)
-            for (int r = 0; r < R; ++r)  // one launch per lattice
-                k_sweep_plain<RULE><<<(unsigned)blocks, 256, 0, s>>>(plain + (int64_t)r * N, g, q, t,
-                                                                      seed + (uint64_t)r);
+        for (int h = 0; h < 2; ++h)
+            for (int r = 0; r < R; ++r) {  // one launch per lattice
+                const uint64_t S = seed + (uint64_t)r;
+                const int q = cycle ? (mixed_first(S, t) ^ h) : h;
+                k_sweep_plain<RULE><<<(unsigned)blocks, 256, 0, s>>>(plain + (int64_t)r * N, g, q, t, S);
+            }
     }
     if (launches) *launches += 2 * n * R;
 }
 
 cudaError_t launch_sweeps_plain(int8_t *plain, int L, int R, uint64_t seed, int rule, int64_t t0, int64_t n,
-                                cudaStream_t s, int64_t *launches)
+                                int cycle, cudaStream_t s, int64_t *launches)
 {
     if (n <= 0) return cudaSuccess;
     const Geom g = make_geom(L);
     switch (rule) {
-    case TIE_GLAUBER: sweeps_plain_rule<TIE_GLAUBER>(plain, g, R, seed, t0, n, s, launches); break;
-    case TIE_ALWAYS: sweeps_plain_rule<TIE_ALWAYS>(plain, g, R, seed, t0, n, s, launches); break;
-    default: sweeps_plain_rule<TIE_NEVER>(plain, g, R, seed, t0, n, s, launches); break;
+    case TIE_GLAUBER: sweeps_plain_rule<TIE_GLAUBER>(plain, g, R, seed, t0, n, cycle, s, launches); break;
+    case TIE_ALWAYS: sweeps_plain_rule<TIE_ALWAYS>(plain, g, R, seed, t0, n, cycle, s, launches); break;
+    default: sweeps_plain_rule<TIE_NEVER>(plain, g, R, seed, t0, n, cycle, s, launches); break;
     }
     return cudaGetLastError();
 }

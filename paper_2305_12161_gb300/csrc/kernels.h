@@ -32,14 +32,19 @@ SweepConfig default_sweep_config(int L, int R);
 
 // n_mcs sweeps from completed-sweep count t0; returns the number of launches through
 // *launches.
+// cycle 0: red then blue every sweep; cycle 1: mixed cycle (random first sublattice per
+// sweep and replica, see mixed_first).
 cudaError_t launch_sweeps_packed(uint32_t *lat, int L, int R, uint64_t seed, int rule, int64_t t0,
-                                 int64_t n_mcs, const SweepConfig &cfg, cudaStream_t s,
+                                 int64_t n_mcs, int cycle, const SweepConfig &cfg, cudaStream_t s,
                                  int64_t *launches);
+int mixed_first(uint64_t S, uint32_t t);
+// Menger-sponge start of iteration k for every replica (padding words must be zero).
+cudaError_t launch_init_menger(uint32_t *lat, int L, int R, uint64_t seed, int k, cudaStream_t s);
 
 // ---- plain form: one byte per spin, replica r at plain + r*N. --------------------
 cudaError_t launch_init_plain(int8_t *plain, int L, int R, uint64_t seed, cudaStream_t s);
 cudaError_t launch_sweeps_plain(int8_t *plain, int L, int R, uint64_t seed, int rule, int64_t t0,
-                                int64_t n_mcs, cudaStream_t s, int64_t *launches);
+                                int64_t n_mcs, int cycle, cudaStream_t s, int64_t *launches);
 // plain -> packed (for the shared measurement kernels) and back.
 cudaError_t launch_pack(const int8_t *plain, uint32_t *lat, int L, int R, cudaStream_t s);
 cudaError_t launch_unpack(const uint32_t *lat, int8_t *plain, int L, int R, cudaStream_t s);

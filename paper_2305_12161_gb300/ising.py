@@ -26,6 +26,7 @@ TIE_GLAUBER, TIE_ALWAYS, TIE_NEVER = 0, 1, 2
 FORM_PACKED, FORM_PLAIN = 0, 1
 MEAS_DEVICE, MEAS_CONNECTED, MEAS_NO_CORR = 1, 2, 4
 PTR_DEVICE = 1
+CYCLE_01, CYCLE_MIXED = 0, 1
 VARIANT_AUTO, VARIANT_WORD, VARIANT_ZMARCH, VARIANT_ZFAST, VARIANT_ZDEEP = 0, 1, 2, 3, 4
 
 
@@ -41,7 +42,7 @@ class IsingError(RuntimeError):
 class ising_opts(ctypes.Structure):
     _fields_ = [("tie", ctypes.c_int), ("form", ctypes.c_int), ("stream", ctypes.c_void_p),
                 ("device", ctypes.c_int), ("variant", ctypes.c_int), ("tile_y", ctypes.c_int),
-                ("tile_z", ctypes.c_int), ("depth", ctypes.c_int)]
+                ("tile_z", ctypes.c_int), ("depth", ctypes.c_int), ("cycle", ctypes.c_int)]
 
 
 def lib_path() -> str:
@@ -64,6 +65,7 @@ def lib() -> ctypes.CDLL:
                                                    ctypes.POINTER(ising_opts)]),
                 "ising_sweep": (ctypes.c_int, [vp, ctypes.c_int64]),
                 "ising_reinit": (ctypes.c_int, [vp, ctypes.c_uint64]),
+                "ising_init_menger": (ctypes.c_int, [vp, ctypes.c_int]),
                 "ising_record_len": (ctypes.c_int64, [ctypes.c_int]),
                 "ising_measure": (ctypes.c_int, [vp, vp]),
                 "ising_measure_ex": (ctypes.c_int, [vp, vp, vp, ctypes.c_double, ctypes.c_uint]),
@@ -157,11 +159,13 @@ class Ising:
     """One context: ``replicas`` lattices of size ``L`` (replica r seeded ``seed + r``)."""
 
     def __init__(self, L: int, replicas: int = 1, seed: int = 1, tie: int = TIE_GLAUBER, form: int = FORM_PACKED,
-                 stream=None, device: int = -1, variant: int = 0, tile_y: int = 0, tile_z: int = 0, depth: int = 0):
+                 stream=None, device: int = -1, variant: int = 0, tile_y: int = 0, tile_z: int = 0, depth: int = 0,
+                 cycle: int = CYCLE_01):
         self._h = ctypes.c_void_p()
         o = ising_opts()
         lib().ising_default_opts(ctypes.byref(o))
         o.tie, o.form, o.device, o.variant, o.tile_y, o.tile_z, o.depth = tie, form, device, variant, tile_y, tile_z, depth
+        o.cycle = cycle
         sh = _stream_handle(stream)
         o.stream = sh if sh else None
         self._stream_obj = stream  # keep the caller's stream alive
@@ -187,6 +191,10 @@ class Ising:
         """Redraw the T = infinity start (replica r: seed + r) and reset t to 0."""
         self._check(lib().ising_reinit(self._h, seed % 2**64), "ising_reinit")
         self.seed = seed
+
+    def init_menger(self, k: int) -> None:
+        """Menger-sponge start of iteration k for every replica; t = 0."""
+        self._check(lib().ising_init_menger(self._h, k), "ising_init_menger")
 
     def sweep(self, n_mcs: int) -> None:
         self._check(lib().ising_sweep(self._h, n_mcs), "ising_sweep")
