@@ -144,7 +144,7 @@ def run_quench_case(args):
     import __graft_entry__
     from paper_2305_12161_gb300 import ising
     __graft_entry__.build()
-    with ising.Ising(args.L, replicas=1, seed=1) as q:
+    with ising.Ising(args.L, replicas=1, seed=1, corr=args.corr) as q:
         q.sweep(args.mcs)
         rec, der = q.measure_ex(c=0.5)
         print(json.dumps({"case": "quench", "L": args.L, "mcs": args.mcs, "B": int(rec[0, 2]),
@@ -274,6 +274,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--L", type=int, default=2048)
     ap.add_argument("--mcs", type=int, default=1000)
+    ap.add_argument("--corr", type=int, default=0, help="correlation method: 0 auto, 1 popcount, 2 tensor cores")
     ap.add_argument("--t-checkpoint", type=int, default=10_000)
     ap.add_argument("--K", type=int, default=4, help="measured times per leg (4: one per decade)")
     ap.add_argument("--ref-L", type=int, default=1024)

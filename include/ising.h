@@ -79,7 +79,18 @@ typedef struct {
     int tile_z;     /* packed z-marching variant: planes per tile (0 = automatic) */
     int depth;      /* variant 4: planes in flight in the copy pipeline, 2..4 (0 = 3) */
     int cycle;      /* ising_cycle: sublattice order of each sweep */
+    int corr;       /* ising_corr: how the correlation sums D_a(r) are computed */
 } ising_opts;
+
+/* Method of the correlation sums (identical results).  POPCOUNT: XOR + bit counts over
+ * packed words, any L.  TENSOR: D_a(r) = N/2 - (1/2) sum_j G[j][j+r] with G the Gram
+ * matrix of the L positions over the L^2 lines of the axis, computed by fp8 warp-level
+ * tensor-core MMAs on +-1 (exact: |G| <= L^2 <= 2^24 in fp32); L a multiple of 128 in
+ * 256..2048; it allocates a scratch of replicas * L^3/8 bytes (the bit-transposed
+ * lattice) at its first use.  AUTO: POPCOUNT (measured faster on GB300: the warp-level
+ * fp8 MMA sustains about 360 TFLOP/s there, which caps the Gram path near the bit-count
+ * path's speed). */
+typedef enum { ISING_CORR_AUTO = 0, ISING_CORR_POPCOUNT = 1, ISING_CORR_TENSOR = 2 } ising_corr;
 
 /* Sublattice order of a sweep.  01: red (q = 0) then blue every sweep (the paper's main
  * runs, Methods).  MIXED: the first sublattice of each sweep is random (Supp. Methods I B,

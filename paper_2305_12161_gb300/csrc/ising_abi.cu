@@ -26,6 +26,7 @@ struct ising_ctx {
     int8_t *plain = nullptr;     // PLAIN form lattice
     int64_t *rec_dev = nullptr;  // R records
     double *der_dev = nullptr;   // R x 4
+    uint32_t *xt = nullptr;      // tensor-core correlation: bit-transposed lattice (lazy)
     int64_t t = 0;
     int poisoned = 0;
     int64_t launches = 0;
@@ -100,6 +101,7 @@ void ising_default_opts(ising_opts *o)
     o->tile_z = 0;
     o->depth = 0;
     o->cycle = 0;
+    o->corr = 0;
 }
 
 int64_t ising_record_len(int L)
@@ -152,6 +154,7 @@ int ising_destroy(ising_ctx *c)
             if (c->plain) cudaFreeAsync(c->plain, c->stream);
             if (c->rec_dev) cudaFreeAsync(c->rec_dev, c->stream);
             if (c->der_dev) cudaFreeAsync(c->der_dev, c->stream);
+            if (c->xt) cudaFreeAsync(c->xt, c->stream);
             cudaStreamSynchronize(c->stream);
         }
         if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -170,6 +173,8 @@ int ising_create_ex(ising_ctx **out, int L, int R, uint64_t seed, const ising_op
     if (L < 4 || L % 2 != 0 || R < 1 || R > 65535) return ISING_EINVAL;
     if (o.tie < 0 || o.tie > 2 || (o.form != ISING_FORM_PACKED && o.form != ISING_FORM_PLAIN)) return ISING_EINVAL;
     if (o.cycle != ISING_CYCLE_01 && o.cycle != ISING_CYCLE_MIXED) return ISING_EINVAL;
+    if (o.corr < ISING_CORR_AUTO || o.corr > ISING_CORR_TENSOR) return ISING_EINVAL;
+    if (o.corr == ISING_CORR_TENSOR && !corr_mma_supported(L)) return ISING_EINVAL;
     // the measurement kernels always run on the packed store
     if (!packed_L_ok(L)) return ISING_EINVAL;
     if ((int64_t)L > 4096) return ISING_EINVAL;  // 32-bit Philox group index bound
@@ -312,7 +317,19 @@ int ising_measure_ex(ising_ctx *c, int64_t *rec, double *derived, double cval, u
         c->launches += 1;
     }
     int64_t *rdst = (dev && rec) ? rec : c->rec_dev;
-    CK(c, launch_measure(c->lat, c->L, c->R, c->t, corr, rdst, c->stream, &c->launches));
+    int method = CORR_NONE;
+    if (corr) {
+        method = CORR_POPCOUNT;
+        if (c->opts.corr == ISING_CORR_TENSOR) method = CORR_TENSOR;
+    }
+    if (method == CORR_TENSOR && !c->xt) {
+        const size_t bytes = (size_t)c->R * (size_t)c->L * c->L * c->L / 8;
+        if (cudaMallocAsync((void **)&c->xt, bytes, c->stream) != cudaSuccess) {
+            c->xt = nullptr;
+            return fail(c, ISING_ENOMEM, "correlation scratch");
+        }
+    }
+    CK(c, launch_measure(c->lat, c->L, c->R, c->t, method, rdst, c->stream, &c->launches, c->xt));
     double *ddst = nullptr;
     if (derived) {
         ddst = dev ? derived : c->der_dev;

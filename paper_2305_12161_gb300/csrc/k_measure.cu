@@ -20,12 +20,22 @@ namespace ising {
 
 __device__ __forceinline__ int64_t rec_len(int L) { return 3 + 3 * (int64_t)(L / 2 + 1); }
 
-__global__ void k_rec_init(int64_t *rec, int L, int R, int64_t t, bool corr)
+// corr: 0 = correlations not measured (-1), 1 = summed from 0, 2 = tensor-core path,
+// which subtracts from N/2 (D_a(0) stays 0).
+__global__ void k_rec_init(int64_t *rec, int L, int R, int64_t t, int corr)
 {
     const int64_t RL = rec_len(L);
+    const int64_t H1 = L / 2 + 1;
+    const int64_t half_n = (int64_t)L * L * L / 2;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < RL * R; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t j = i % RL;
-        rec[i] = j == 0 ? t : (j < 3 ? 0 : (corr ? 0 : -1));
+        int64_t v;
+        if (j == 0) v = t;
+        else if (j < 3) v = 0;
+        else if (corr == 0) v = -1;
+        else if (corr == 2 && (j - 3) % H1 != 0) v = half_n;
+        else v = 0;
+        rec[i] = v;
     }
 }
 
@@ -297,8 +307,8 @@ static cudaError_t launch_corr(const uint32_t *lat, const Geom &g, int R, int64_
     return cudaGetLastError();
 }
 
-cudaError_t launch_measure(const uint32_t *lat, int L, int R, int64_t t, bool corr, int64_t *rec, cudaStream_t s,
-                           int64_t *launches)
+cudaError_t launch_measure(const uint32_t *lat, int L, int R, int64_t t, int corr, int64_t *rec, cudaStream_t s,
+                           int64_t *launches, uint32_t *xt_scratch)
 {
     const Geom g = make_geom(L);
     const int64_t RL = 3 + 3 * (int64_t)(L / 2 + 1);
@@ -309,7 +319,12 @@ cudaError_t launch_measure(const uint32_t *lat, int L, int R, int64_t t, bool co
     if (mb > 152 * 8) mb = 152 * 8;
     k_mb<<<dim3((unsigned)mb, (unsigned)R), 256, 0, s>>>(lat, g, rec);
     int n = 2;
-    if (corr) {
+    if (corr == CORR_TENSOR) {
+        if (!xt_scratch || !corr_mma_supported(L)) return cudaErrorInvalidValue;
+        const cudaError_t e = launch_corr_mma(lat, L, R, rec, xt_scratch, s, nullptr);
+        if (e != cudaSuccess) return e;
+        n += 2;
+    } else if (corr) {
         const cudaError_t e = corr_rt(L) == 8 ? launch_corr<8>(lat, g, R, rec, s) : launch_corr<4>(lat, g, R, rec, s);
         if (e != cudaSuccess) return e;
         ++n;

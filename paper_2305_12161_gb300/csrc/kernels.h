@@ -50,10 +50,15 @@ cudaError_t launch_pack(const int8_t *plain, uint32_t *lat, int L, int R, cudaSt
 cudaError_t launch_unpack(const uint32_t *lat, int8_t *plain, int L, int R, cudaStream_t s);
 
 // ---- measurement on the packed store ----------------------------------------------
-// rec: R records of 3 + 3*(L/2+1) int64 (must not alias lat).  Writes t, M, B and,
-// if corr, D_a(r); otherwise D_a(r) = -1.
-cudaError_t launch_measure(const uint32_t *lat, int L, int R, int64_t t, bool corr, int64_t *rec,
-                           cudaStream_t s, int64_t *launches);
+// rec: R records of 3 + 3*(L/2+1) int64 (must not alias lat).  Writes t, M, B and the
+// correlation sums D_a(r) by the chosen method (CORR_NONE writes D_a(r) = -1).
+// CORR_TENSOR needs corr_mma_supported(L) and xt_scratch of R * L^3 / 8 bytes.
+enum CorrMethod : int { CORR_NONE = 0, CORR_POPCOUNT = 1, CORR_TENSOR = 2 };
+cudaError_t launch_measure(const uint32_t *lat, int L, int R, int64_t t, int corr, int64_t *rec,
+                           cudaStream_t s, int64_t *launches, uint32_t *xt_scratch = nullptr);
+bool corr_mma_supported(int L);
+cudaError_t launch_corr_mma(const uint32_t *lat, int L, int R, int64_t *rec, uint32_t *xt_scratch, cudaStream_t s,
+                            int64_t *launches);
 // derived: R x [e, m, l_E, l_C]
 cudaError_t launch_derived(const int64_t *rec, int L, int R, double c, bool connected, double *derived,
                            cudaStream_t s, int64_t *launches);

@@ -214,3 +214,35 @@ def test_reinit_equals_fresh_context(ising):
     with ising.Ising(64, replicas=2, seed=8) as b:
         b.sweep(3)
         assert np.array_equal(b.measure(), ra)
+
+
+@pytest.mark.parametrize("L", [256, 384, 512, 1024])
+def test_tensor_core_correlation_equals_popcount(ising, L):
+    R = 2 if L <= 512 else 1
+    with ising.Ising(L, replicas=R, seed=3, corr=ising.CORR_POPCOUNT) as a, \
+            ising.Ising(L, replicas=R, seed=3, corr=ising.CORR_TENSOR) as b:
+        for n in (0, 3, 20):
+            a.sweep(n)
+            b.sweep(n)
+            ra, rb = a.measure(), b.measure()
+            assert np.array_equal(ra, rb), n
+            # two measurements in a row reuse the scratch and give the same record
+            assert np.array_equal(b.measure(), rb)
+
+
+def test_tensor_core_correlation_closed_forms(ising):
+    L = 256
+    states = [inputs.neel_state(L), inputs.stripe_state(L, 8, "x"), inputs.stripe_state(L, 3, "z", 1),
+              inputs.uniform_state(L, -1)]
+    with ising.Ising(L, replicas=len(states), seed=1, corr=ising.CORR_TENSOR) as q:
+        for r, s in enumerate(states):
+            q.set_spins(s, r)
+        rec, der = q.measure_ex()
+    for r, s in enumerate(states):
+        want = oracle.record(s, 0)
+        assert np.array_equal(rec[r], want), r
+
+
+def test_tensor_core_correlation_rejects_unsupported_sizes(ising):
+    with pytest.raises(ising.IsingError):
+        ising.Ising(64, replicas=1, seed=1, corr=ising.CORR_TENSOR)
