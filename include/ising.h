@@ -198,7 +198,10 @@ int64_t ising_launch_count(const ising_ctx *ctx);
  * persistent cooperative kernel launch over a CTA work list: lattices small enough
  * for one CTA's shared memory (e.g. 64^3 = 32 KiB packed) are owned whole by one CTA
  * and swept there; larger ones are split into slabs over a group of CTAs that meet at
- * a bounded barrier in global memory between half-sweeps.  Every lattice follows
+ * a bounded barrier in global memory between half-sweeps.  Classes with L a multiple of
+ * 256 and at least the streaming threshold (default 256; ising_batch_set_streamed) are
+ * instead swept in the same segment by the single-lattice z-marching kernel, which
+ * streams them faster than slab groups do.  Every lattice follows
  * exactly the trajectory of the single-lattice entry points (same rule, order and
  * random bits), so batching changes speed, not results.
  * Records and derived values are concatenated in class order, replica-major within a
@@ -234,6 +237,12 @@ int ising_batch_plan(const ising_batch *b, int *ntasks, int *nlocal, int *ngroup
  * rebuild the work list; *w_local_out receives the chosen weight. */
 int ising_batch_tune(ising_batch *b, int probe_mcs, double *w_local_out);
 int ising_batch_set_weights(ising_batch *b, double w_local, double w_group);
+/* Classes with L >= min_L and L % 256 == 0 are swept by the z-marching kernel, the
+ * others by the persistent kernel; min_L <= 0 puts every class in the persistent kernel.
+ * Rebuilds the work list (results are unchanged). */
+int ising_batch_set_streamed(ising_batch *b, int min_L);
+/* Number of classes currently swept by the z-marching kernel. */
+int ising_batch_streamed_classes(const ising_batch *b);
 /* Failure injection for tests: CTA `cta` returns at once, so its slab group's barrier
  * waits run out after timeout_s; the segment then ends early and the next
  * synchronising call returns ISING_ETIMEOUT (the batch is poisoned).  cta = -1 clears. */

@@ -24,6 +24,8 @@ struct BatchClass {
     uint32_t *lat;       // R * 2 * nw words
     int64_t rec_off;     // offset of this class's records in a batch record block
     int64_t der_off;     // offset (in replicas) of this class's derived rows
+    int streamed;        // swept by the z-marching kernel instead of the persistent one
+    SweepConfig cfg;     // its kernel configuration
 };
 
 bool packed_L_ok(int L) { return (L >= 64 && L % 64 == 0) || L == 4 || L == 8 || L == 16 || L == 32; }
@@ -54,6 +56,7 @@ struct ising_batch {
     double w_local = 1.0, w_group = 1.0;
     uint64_t timeout_ns = 2000000000ull;
     int missing_cta = -1;
+    int stream_min_L = 256;  // classes with L >= this (and L % 256 == 0) are streamed
     // measurement scratch
     int64_t *d_rec = nullptr;
     double *d_der = nullptr;
@@ -171,11 +174,14 @@ int upload_plan(ising_batch *b)
     b->d_barriers = nullptr;
     b->d_cta_ns = nullptr;
     const size_t nt = b->h_tasks.size();
-    if (cudaMalloc(&b->d_tasks, nt * sizeof(BatchTask)) != cudaSuccess) return ISING_ENOMEM;
+    if (cudaMalloc(&b->d_tasks, std::max<size_t>(1, nt) * sizeof(BatchTask)) != cudaSuccess) return ISING_ENOMEM;
     if (cudaMalloc(&b->d_barriers, sizeof(unsigned) * (size_t)std::max(1, b->ngroups)) != cudaSuccess)
         return ISING_ENOMEM;
-    if (cudaMalloc(&b->d_cta_ns, nt * sizeof(unsigned long long)) != cudaSuccess) return ISING_ENOMEM;
-    BCK(b, cudaMemcpyAsync(b->d_tasks, b->h_tasks.data(), nt * sizeof(BatchTask), cudaMemcpyHostToDevice, b->stream));
+    if (cudaMalloc(&b->d_cta_ns, std::max<size_t>(1, nt) * sizeof(unsigned long long)) != cudaSuccess)
+        return ISING_ENOMEM;
+    if (nt)
+        BCK(b, cudaMemcpyAsync(b->d_tasks, b->h_tasks.data(), nt * sizeof(BatchTask), cudaMemcpyHostToDevice,
+                               b->stream));
     BCK(b, cudaStreamSynchronize(b->stream));
     if (b->gexec) {
         cudaGraphExecDestroy(b->gexec);
@@ -190,10 +196,17 @@ int enqueue_segment(ising_batch *b, int64_t n, unsigned long long *cta_ns)
 {
     while (n > 0) {
         const int chunk = (int)std::min<int64_t>(n, 1 << 30);
-        BCK(b, cudaMemsetAsync(b->d_barriers, 0, sizeof(unsigned) * (size_t)std::max(1, b->ngroups), b->stream));
-        BCK(b, launch_batch(b->d_tasks, (int)b->h_tasks.size(), b->d_lats, b->rule, (uint32_t)b->t, chunk,
-                            b->d_barriers, b->d_status, b->timeout_ns, b->missing_cta, cta_ns, b->smem, b->stream));
-        b->launches += 1;
+        if (!b->h_tasks.empty()) {
+            BCK(b, cudaMemsetAsync(b->d_barriers, 0, sizeof(unsigned) * (size_t)std::max(1, b->ngroups), b->stream));
+            BCK(b, launch_batch(b->d_tasks, (int)b->h_tasks.size(), b->d_lats, b->rule, (uint32_t)b->t, chunk,
+                                b->d_barriers, b->d_status, b->timeout_ns, b->missing_cta, cta_ns, b->smem,
+                                b->stream));
+            b->launches += 1;
+        }
+        for (const auto &k : b->cls)
+            if (k.streamed)
+                BCK(b, launch_sweeps_packed(k.lat, k.L, k.R, k.seed, b->rule, b->t, chunk, 0, k.cfg, b->stream,
+                                            &b->launches));
         b->t += chunk;
         n -= chunk;
     }
@@ -221,9 +234,58 @@ int read_status(ising_batch *b)
     return ISING_OK;
 }
 
+// Split the classes between the persistent kernel and the z-marching kernel, rebuild the
+// persistent kernel's lattice list, shared-memory size, occupancy and work list.
+int assign_modes(ising_batch *b)
+{
+    b->h_lats.clear();
+    int max_local = 0;
+    for (auto &k : b->cls) {
+        k.streamed = b->stream_min_L > 0 && k.L >= b->stream_min_L && k.L % 256 == 0;
+        k.cfg = default_sweep_config(k.L, k.R);
+        if (k.streamed) continue;
+        const Geom g = make_geom(k.L);
+        for (int r = 0; r < k.R; ++r)
+            b->h_lats.push_back(BatchLattice{k.lat + (int64_t)r * 2 * g.nw, k.seed + (uint64_t)r, k.L, 0});
+        if (lattice_bytes(k.L) <= 96 * 1024) max_local = std::max<int>(max_local, (int)lattice_bytes(k.L));
+    }
+    cudaFree(b->d_lats);
+    b->d_lats = nullptr;
+    if (cudaMalloc(&b->d_lats, sizeof(BatchLattice) * std::max<size_t>(1, b->h_lats.size())) != cudaSuccess)
+        return ISING_ENOMEM;
+    if (!b->h_lats.empty())
+        BCK(b, cudaMemcpyAsync(b->d_lats, b->h_lats.data(), sizeof(BatchLattice) * b->h_lats.size(),
+                               cudaMemcpyHostToDevice, b->stream));
+    b->smem = max_local;
+    BCK(b, batch_occupancy(std::max(b->smem, 0), &b->occ));
+    if (b->occ < 1) return bfail(b, ISING_ECUDA, "batch kernel does not fit an SM");
+    b->capacity = b->occ * b->sms;
+    int s = build_plan(b);
+    if (s != ISING_OK) return s;
+    return upload_plan(b);
+}
+
 }  // namespace
 
 extern "C" {
+
+int ising_batch_set_streamed(ising_batch *b, int min_L)
+{
+    int s = bcheck(b);
+    if (s) return s;
+    DevGuard dg(b->device);
+    BCK(b, cudaStreamSynchronize(b->stream));
+    b->stream_min_L = min_L;
+    return assign_modes(b);
+}
+
+int ising_batch_streamed_classes(const ising_batch *b)
+{
+    if (!b) return -1;
+    int n = 0;
+    for (const auto &k : b->cls) n += k.streamed;
+    return n;
+}
 
 int ising_batch_destroy(ising_batch *b)
 {
@@ -279,9 +341,8 @@ int ising_batch_create(ising_batch **out, int nclass, const int *L, const int *r
         b->own_stream = true;
     }
     int64_t rec_off = 0, der_off = 0;
-    int max_local = 0;
     for (int c = 0; c < nclass; ++c) {
-        BatchClass k{L[c], replicas[c], seeds[c], nullptr, rec_off, der_off};
+        BatchClass k{L[c], replicas[c], seeds[c], nullptr, rec_off, der_off, 0, SweepConfig{VARIANT_WORD, 0, 0, 0}};
         const int64_t bytes = lattice_bytes(L[c]) * replicas[c];
         if (cudaMalloc(&k.lat, (size_t)bytes) != cudaSuccess) {
             b->cls.push_back(k);
@@ -294,30 +355,17 @@ int ising_batch_create(ising_batch **out, int nclass, const int *L, const int *r
         }
         b->launches += 1;
         b->cls.push_back(k);
-        const Geom g = make_geom(L[c]);
-        for (int r = 0; r < replicas[c]; ++r)
-            b->h_lats.push_back(BatchLattice{k.lat + (int64_t)r * 2 * g.nw, seeds[c] + (uint64_t)r, L[c], 0});
         rec_off += ising_record_len(L[c]) * replicas[c];
         der_off += replicas[c];
-        if (lattice_bytes(L[c]) <= 96 * 1024) max_local = std::max<int>(max_local, (int)lattice_bytes(L[c]));
     }
-    b->nlat = (int64_t)b->h_lats.size();
+    b->nlat = der_off;
     b->rec_words = rec_off;
-    if (cudaMalloc(&b->d_lats, sizeof(BatchLattice) * b->h_lats.size()) != cudaSuccess) return bail(ISING_ENOMEM);
-    if (cudaMemcpyAsync(b->d_lats, b->h_lats.data(), sizeof(BatchLattice) * b->h_lats.size(), cudaMemcpyHostToDevice,
-                        b->stream) != cudaSuccess)
-        return bail(ISING_ECUDA);
     if (cudaMalloc(&b->d_status, sizeof(int)) != cudaSuccess) return bail(ISING_ENOMEM);
     if (cudaMemsetAsync(b->d_status, 0, sizeof(int), b->stream) != cudaSuccess) return bail(ISING_ECUDA);
     if (cudaMalloc(&b->d_rec, sizeof(int64_t) * (size_t)b->rec_words) != cudaSuccess) return bail(ISING_ENOMEM);
     if (cudaMalloc(&b->d_der, sizeof(double) * 4 * (size_t)b->nlat) != cudaSuccess) return bail(ISING_ENOMEM);
-    // shared memory per CTA: room for the largest lattice kept whole in a LOCAL task
-    b->smem = max_local;
     if (cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return bail(ISING_ECUDA);
-    if (batch_occupancy(std::max(b->smem, 0), &b->occ) != cudaSuccess || b->occ < 1) return bail(ISING_ECUDA);
-    b->capacity = b->occ * b->sms;
-    if (build_plan(b) != ISING_OK) return bail(ISING_EINVAL);
-    int s = upload_plan(b);
+    int s = assign_modes(b);
     if (s != ISING_OK) return bail(s);
     *out = b;
     return ISING_OK;
@@ -506,7 +554,7 @@ int ising_batch_tune(ising_batch *b, int probe_mcs, double *w_local_out)
     // Probe rounds: run a short segment, read each CTA's elapsed time, and set the LOCAL
     // weight to the measured ratio of time per spin (LOCAL vs GROUP); rebuild the plan.
     // The probe advances the batch (the state stays a valid trajectory: t moves on).
-    for (int round = 0; round < 3; ++round) {
+    for (int round = 0; round < 3 && !b->h_tasks.empty(); ++round) {
         if ((s = enqueue_segment(b, probe_mcs, b->d_cta_ns)) != ISING_OK) return s;
         std::vector<unsigned long long> ns(b->h_tasks.size());
         BCK(b, cudaMemcpyAsync(ns.data(), b->d_cta_ns, sizeof(unsigned long long) * ns.size(), cudaMemcpyDeviceToHost,

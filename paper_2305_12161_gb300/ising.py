@@ -100,6 +100,8 @@ def lib() -> ctypes.CDLL:
                 "ising_batch_plan": (ctypes.c_int, [vp, vp, vp, vp, vp]),
                 "ising_batch_tune": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
                 "ising_batch_set_weights": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_double]),
+                "ising_batch_set_streamed": (ctypes.c_int, [vp, ctypes.c_int]),
+                "ising_batch_streamed_classes": (ctypes.c_int, [vp]),
                 "ising_batch_inject_missing_cta": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_double]),
                 "ising_batch_last_error": (ctypes.c_char_p, [vp]),
                 "ising_batch_launch_count": (ctypes.c_int64, [vp]),
@@ -400,6 +402,13 @@ class Batch:
 
     def set_weights(self, w_local: float, w_group: float = 1.0) -> None:
         self._check(lib().ising_batch_set_weights(self._h, w_local, w_group), "ising_batch_set_weights")
+
+    def set_streamed(self, min_L: int) -> None:
+        """Classes with L >= min_L (L % 256 == 0) use the z-marching kernel; <= 0: none."""
+        self._check(lib().ising_batch_set_streamed(self._h, min_L), "ising_batch_set_streamed")
+
+    def streamed_classes(self) -> int:
+        return int(lib().ising_batch_streamed_classes(self._h))
 
     def inject_missing_cta(self, cta: int, timeout_s: float = 1.0) -> None:
         self._check(lib().ising_batch_inject_missing_cta(self._h, cta, timeout_s), "ising_batch_inject_missing_cta")

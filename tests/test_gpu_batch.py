@@ -45,12 +45,18 @@ def test_small_batch_matches_oracle_at_every_time(ising):
                     assert np.array_equal(b.get_packed(ci, r), q.get_packed(0)), (L, r)
 
 
-def test_batch_matches_single_contexts_large(ising):
+@pytest.mark.parametrize("streamed", [256, 0])
+def test_batch_matches_single_contexts_large(ising, streamed):
     classes = [(64, 8, 1), (192, 2, 5), (256, 2, 9), (512, 1, 11)]
     n = 9
     with ising.Batch(classes) as b:
+        b.set_streamed(streamed)
         plan = b.plan()
-        assert plan["groups"] >= 3 and plan["ctas"] <= plan["capacity"]
+        if streamed:
+            assert b.streamed_classes() == 2 and plan["groups"] >= 1
+        else:
+            assert b.streamed_classes() == 0 and plan["groups"] >= 3
+        assert plan["ctas"] <= plan["capacity"]
         b.sweep(n)
         rec, der = b.measure_ex()
         for ci, (L, R, seed) in enumerate(classes):
@@ -126,7 +132,7 @@ def test_tuned_plan_changes_speed_not_results(ising):
 
 def test_missing_group_member_times_out_instead_of_hanging(ising):
     import time
-    with ising.Batch([(256, 1, 1)]) as b:
+    with ising.Batch([(128, 1, 1)]) as b:
         plan = b.plan()
         assert plan["groups"] == 1 and plan["ctas"] > 1
         b.inject_missing_cta(0, timeout_s=0.5)
