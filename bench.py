@@ -430,7 +430,15 @@ def main():
     corr_ops = 3 * (L // 2) * (N // 32)
     n_meas = len(meas_events)
     meas_avg_s = meas_ms * 1e-3 / n_meas
-    popc_peak = 152 * 16 * pk["sm_max_mhz"] * 1e6 / 1e12  # T popc/s: 16 POPC lanes per SM per clock
+    # Bound of the correlation kernel, which sums XOR words on two pipes at once.  Counted from
+    # the source: a POPC-path word is 1 bit count (16 lanes per SM per clock) + 2 logic/add
+    # ops (64 lanes per SM per clock); a carry-save word is 1/8 bit count + 23/8 logic/add ops
+    # (8 XORs, 7 adders of two 3-input ops each, 1 add per 8 words).  The best split f of
+    # words on the POPC path balances both pipes; it gives 26.7 words per SM per clock.
+    p_pop, a_pop, p_csa, a_csa = 1.0, 2.0, 1.0 / 8, 23.0 / 8
+    f_pop = (a_csa / 64 - p_csa / 16) / ((p_pop - p_csa) / 16 + (a_csa - a_pop) / 64)
+    words_per_clk = 16 / (f_pop * p_pop + (1 - f_pop) * p_csa)
+    popc_peak = 152 * words_per_clk * pk["sm_max_mhz"] * 1e6 / 1e12  # T word pairs/s
     corr_tops = corr_ops / meas_avg_s / 1e12
     kname = {1: "k_sweep_word", 2: "k_sweep_zmarch", 3: "k_sweep_zfast", 4: "k_sweep_zdeep"}[tuned["variant"]]
     # DRAM bytes per launch from one ncu capture of the same kernel at L=2048 (sweep t=2);
@@ -441,7 +449,7 @@ def main():
                   "peak_src": pk["src"], "avg_launch_ms": sweep_avg_s * 1e3, "bytes_per_launch": bytes_per_launch,
                   "updates_per_ns": (N // 2) / sweep_avg_s / 1e9}
     roof_corr = {"kernel": "k_corr + k_mb (one measurement)", "bound": "alu", "achieved": corr_tops,
-                 "peak": popc_peak, "unit": "Tpopc/s", "frac": corr_tops / popc_peak, "traffic": None,
+                 "peak": popc_peak, "unit": "T XOR-word-pairs/s", "frac": corr_tops / popc_peak, "traffic": None,
                  "avg_launch_ms": meas_avg_s * 1e3, "ops_per_launch": corr_ops}
     roof = roof_sweep if sweep_ms >= meas_ms else roof_corr
     e2e = None

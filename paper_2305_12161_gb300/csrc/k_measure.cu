@@ -206,10 +206,12 @@ __global__ void __launch_bounds__(NT) k_corr(const uint32_t *lat, Geom g, int64_
             unsigned int total[RT];
             // Two ways to sum the XOR words, each saturating a different pipe: POPC per
             // word (bound by the 16-lane/clk bit-count unit) or carry-save adders (bound by
-            // the ALU).  Warps 5..7 of every 8 take the carry-save path so that both pipes
-            // work at once; the choice is per warp, so no warp diverges.  (Choosing per
-            // item instead, so every warp alternates, measured 7% slower.)
-            if (RT == 8 && (wid & 7) >= 5) {
+            // the ALU).  Warps 4..7 of every 8 take the carry-save path: warps w and w+4 share
+            // an SM sub-partition, so each sub-partition runs one warp of each kind and both
+            // pipes work at once; the choice is per warp, so no warp diverges.  (Measured at
+            // L=2048: 4 of 8 on carry-save 148 ms, 3 of 8 166 ms, none 178 ms, per-item
+            // alternation 7% slower than 3 of 8.)
+            if (RT == 8 && (wid & 7) >= 4) {
                 // Harley-Seal carry-save accumulation per lag: eight XOR words pass through
                 // seven carry-save adders into (ones, twos, fours) and one "eights" word,
                 // so one POPC covers eight words.
