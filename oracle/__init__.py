@@ -90,6 +90,13 @@ def lib() -> ctypes.CDLL:
             L.orc_sweeps_mixed.argtypes = [ctypes.c_int, i8p, ctypes.c_uint32, ctypes.c_int64,
                                            ctypes.c_uint64, ctypes.c_int]
             L.orc_sweeps_mixed.restype = None
+            L.orc_dcb_valid.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+            L.orc_dcb_valid.restype = ctypes.c_int
+            L.orc_dcb_fine_first.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int64]
+            L.orc_dcb_fine_first.restype = ctypes.c_int
+            L.orc_sweeps_dcb.argtypes = [ctypes.c_int, i8p, ctypes.c_uint32, ctypes.c_int64, ctypes.c_uint64,
+                                         ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+            L.orc_sweeps_dcb.restype = ctypes.c_int
             L.orc_derived.argtypes = [ctypes.c_int, i64p, ctypes.c_double, ctypes.c_int, f64p]
             L.orc_derived.restype = None
             _lib = L
@@ -172,6 +179,26 @@ def mixed_order(S: int, t: int) -> int:
 def sweeps_mixed(s: np.ndarray, t0: int, n: int, S: int, rule: int = TIE_GLAUBER) -> None:
     L = _check_lattice(s)
     lib().orc_sweeps_mixed(L, _p(s, ctypes.c_int8), t0, n, S % 2**64, rule)
+
+
+def dcb_valid(L: int, block) -> bool:
+    """True when blocks of ``block = (bx, by, bz)`` sites tile an L^3 lattice as a double checkerboard."""
+    bx, by, bz = block
+    return bool(lib().orc_dcb_valid(L, bx, by, bz))
+
+
+def dcb_fine_first(S: int, t: int, beta: int) -> int:
+    """Parity of the sites block ``beta`` updates first in sweep t of the mixed double checkerboard."""
+    return int(lib().orc_dcb_fine_first(S % 2**64, t, beta))
+
+
+def sweeps_dcb(s: np.ndarray, t0: int, n: int, S: int, block, rule: int = TIE_GLAUBER,
+               mixed: bool = False) -> None:
+    """n double-checkerboard sweeps (Supp. Methods I A; mixed cycle per I B) with blocks ``(bx, by, bz)``."""
+    L = _check_lattice(s)
+    bx, by, bz = block
+    if lib().orc_sweeps_dcb(L, _p(s, ctypes.c_int8), t0, n, S % 2**64, rule, bx, by, bz, int(bool(mixed))) != 0:
+        raise ValueError(f"blocks {block} do not tile L={L} as a double checkerboard")
 
 
 def record_len(L: int) -> int:

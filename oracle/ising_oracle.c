@@ -381,3 +381,84 @@ void orc_sweeps_mixed(int L, int8_t *s, uint32_t t0, int64_t n, uint64_t S, int 
         orc_half_sweep(L, s, 1 - first, t, S, rule, NULL, NULL);
     }
 }
+
+/* ------------------------------------------------------------------------------ */
+/* Double-checkerboard update (Supp. Methods I A: Weigel's GPU domain decomposition,
+ * generalised to d = 3).  The lattice is cut into blocks of bx*by*bz sites; block
+ * (i, j, k) = (x / bx, y / by, z / bz) is red (colour 0) when i + j + k is even and blue
+ * (colour 1) otherwise.  With an even number of blocks along every axis that is cut (or a
+ * single block spanning the axis), two blocks of one colour never share a face, so all
+ * blocks of a colour can be updated at once.  One sweep: for each colour in turn, every
+ * block of that colour updates its sites of one fine sublattice (parity of x + y + z) all
+ * at once, and then the sites of the other parity; sites in other blocks keep their values
+ * during that colour's pass.
+ *
+ * 01 cycle (the steps listed in I A): red blocks first, and in every block the sites of
+ * odd parity first (the darker sites of the paper's 2-d example figure are those with
+ * x + y odd).  Mixed cycle (I B): the first colour is drawn once per sweep with
+ * orc_mixed_order (blue first when it is 1), and the first fine sublattice independently
+ * for every block and sweep: block beta = i + nbx*(j + nby*k) starts with the sites of
+ * parity 1 when bit (beta & 31) of word ((beta >> 5) & 3) of
+ * Philox(counter (beta >> 7, t, 6, 0), key S) is 1, else with those of parity 0.
+ * A site's zero-energy decision uses the same random bit as in the checkerboard update
+ * (phase = its parity, counter word = its compressed index), so the schemes differ only
+ * in the order in which the proposals are made. */
+int orc_dcb_valid(int L, int bx, int by, int bz)
+{
+    const int b[3] = {bx, by, bz};
+    if (L < 2 || (L & 1)) return 0;
+    for (int a = 0; a < 3; ++a) {
+        if (b[a] < 1 || L % b[a] != 0) return 0;
+        const int nb = L / b[a];
+        if (nb != 1 && (nb & 1)) return 0;
+    }
+    return 1;
+}
+
+int orc_dcb_fine_first(uint64_t S, uint32_t t, int64_t beta)
+{
+    uint32_t ctr[4] = {(uint32_t)(beta >> 7), t, 6u, 0u};
+    uint32_t key[2] = {(uint32_t)(S & 0xffffffffu), (uint32_t)(S >> 32)};
+    uint32_t o[4];
+    orc_philox4x32_10(ctr, key, o);
+    return (int)((o[(beta >> 5) & 3] >> (beta & 31)) & 1u);
+}
+
+/* Every site of parity q inside the block with corner (x0, y0, z0), proposed once.  The
+ * sites of one parity are not neighbours of one another, so updating them one after the
+ * other in place gives the same result as updating them all at once. */
+static void dcb_block_pass(int64_t L, int8_t *s, int64_t x0, int64_t y0, int64_t z0, int64_t bx, int64_t by,
+                           int64_t bz, int q, uint32_t t, uint64_t S, int rule)
+{
+    for (int64_t z = z0; z < z0 + bz; ++z)
+        for (int64_t y = y0; y < y0 + by; ++y)
+            for (int64_t x = x0; x < x0 + bx; ++x) {
+                if (((x + y + z) & 1) != q) continue;
+                s[site(L, x, y, z)] = site_new_value(L, s, x, y, z, q, t, S, rule, NULL);
+            }
+}
+
+int orc_sweeps_dcb(int L_, int8_t *s, uint32_t t0, int64_t n, uint64_t S, int rule, int bx, int by, int bz,
+                   int mixed)
+{
+    if (!orc_dcb_valid(L_, bx, by, bz)) return -1;
+    const int64_t L = L_;
+    const int64_t nbx = L / bx, nby = L / by, nbz = L / bz;
+    const int64_t nblocks = nbx * nby * nbz;
+    for (int64_t k = 0; k < n; ++k) {
+        const uint32_t t = t0 + (uint32_t)k;
+        const int first = mixed ? orc_mixed_order(S, t) : 0;
+        for (int pass = 0; pass < 2; ++pass) {
+            const int colour = first ^ pass;
+#pragma omp parallel for schedule(dynamic, 1)
+            for (int64_t beta = 0; beta < nblocks; ++beta) {
+                const int64_t i = beta % nbx, j = (beta / nbx) % nby, kk = beta / (nbx * nby);
+                if (((i + j + kk) & 1) != colour) continue;
+                const int f0 = mixed ? orc_dcb_fine_first(S, t, beta) : 1;
+                dcb_block_pass(L, s, i * bx, j * by, kk * bz, bx, by, bz, f0, t, S, rule);
+                dcb_block_pass(L, s, i * bx, j * by, kk * bz, bx, by, bz, 1 - f0, t, S, rule);
+            }
+        }
+    }
+    return 0;
+}
