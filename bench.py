@@ -238,6 +238,65 @@ def run_batch_case(args):
         print(json.dumps({"case": "batch", "mcs": args.mcs, "plan": b.plan(), "launches": b.launch_count()}))
 
 
+def run_dcb_case(args):
+    """The double-checkerboard sweep (Supp. Methods I A) on one L^3 lattice from the T = inf
+    start: 3 warm-up MCS, then --mcs MCS timed with CUDA events on the context stream, the
+    checkerboard sweep timed the same way beside it.  The roofline counts, per colour
+    launch, the algorithmic bytes of the blocks of one colour: both sublattices of every
+    block row and halo row read once, both sublattices of every block row written once."""
+    import torch
+
+    import __graft_entry__
+    from paper_2305_12161_gb300 import ising
+    __graft_entry__.build()
+    L, mcs = args.L, args.mcs
+    by, bz = args.block_y, args.block_z
+    N = L**3
+    stream = torch.cuda.Stream()
+    pk = _peaks()
+
+    def timed(q, n):
+        q.sweep(3)
+        q.sync()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        l0 = q.launch_count()
+        a.record(stream)
+        q.sweep(n)
+        b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b), q.launch_count() - l0
+
+    clocks = ClockSampler(0)
+    clocks.start()
+    with ising.Ising(L, seed=1, scheme=ising.SCHEME_DOUBLE, block=(0, by, bz), stream=stream) as q:
+        ms, launches = timed(q, mcs)
+    with ising.Ising(L, seed=1, stream=stream, variant=3 if L % 256 == 0 and L <= 2048 else 0) as q:
+        ms_cb, _ = timed(q, mcs)
+    clk = clocks.stop()
+    W = max(1, L // 64)
+    rows_own = L * L  # every row of the lattice belongs to exactly one block
+    nblk = (L // by) * (L // bz)
+    halo_rows = nblk * ((2 * bz if by < L else 0) + (2 * by if bz < L else 0))
+    bytes_mcs = 2 * 4 * W * (rows_own + halo_rows) + 2 * 4 * W * rows_own
+    per_launch_s = ms * 1e-3 / launches
+    bytes_launch = bytes_mcs / 2
+    achieved = bytes_launch / per_launch_s / 1e9
+    print(json.dumps({
+        "case": "dcb", "metric": "spin updates/ns, double-checkerboard sweep (Supp. Methods I A), one GB300",
+        "value": mcs * N / (ms * 1e-3) / 1e9, "unit": UNIT, "higher_is_better": True,
+        "config": {"workload": f"L={L} single lattice, T=inf start + 3 MCS, then {mcs} MCS timed",
+                   "block": [L, by, bz], "cycle": "01", "l2": "lattice larger than L2" if N // 8 > 129e6 else "in L2"},
+        "ms_per_mcs": ms / mcs, "launches": launches,
+        "roofline": {"kernel": "k_sweep_dcb_rows (one colour)", "bound": "hbm", "achieved": achieved,
+                     "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
+                     # DRAM bytes of one launch in one ncu capture (L=2048, 16 x 8 blocks, sweep t=2)
+                     "traffic": 1.2026e9 if (L, by, bz) == (2048, 16, 8) else None,
+                     "avg_launch_ms": per_launch_s * 1e3, "bytes_per_launch": bytes_launch},
+        "checkerboard_updates_per_ns": mcs * N / (ms_cb * 1e-3) / 1e9, "checkerboard_ms_per_mcs": ms_cb / mcs,
+        "clocks": clk}))
+
+
 def run_serve_case(args):
     """Continuous-batching serving on a finite seeded trace: Poisson arrivals at 20/s,
     L log-uniform on {64..1024}, t_max = 10^U[3,5] MCS, 1-16 replicas, 12 log-spaced
@@ -281,7 +340,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
-    ap.add_argument("--case", default="bench", choices=["bench", "quench", "serve", "batch"],
+    ap.add_argument("--block-y", type=int, default=16, help="dcb case: block rows along y")
+    ap.add_argument("--block-z", type=int, default=8, help="dcb case: block planes along z")
+    ap.add_argument("--case", default="bench", choices=["bench", "quench", "serve", "batch", "dcb"],
                     help="quench: init + --mcs sweeps + one measurement, untimed (for profilers); "
                          "serve: the serving loop on the first --requests arrivals of the seeded trace")
     ap.add_argument("--requests", type=int, default=24)
@@ -297,6 +358,9 @@ def main():
         return
     if args.case == "batch":
         run_batch_case(args)
+        return
+    if args.case == "dcb":
+        run_dcb_case(args)
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

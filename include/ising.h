@@ -80,6 +80,10 @@ typedef struct {
     int depth;      /* variant 4: planes in flight in the copy pipeline, 2..4 (0 = 3) */
     int cycle;      /* ising_cycle: sublattice order of each sweep */
     int corr;       /* ising_corr: how the correlation sums D_a(r) are computed */
+    int scheme;     /* ising_scheme: checkerboard or double checkerboard */
+    int block_x;    /* double checkerboard: block sides in sites (0 = default: block_x = L, */
+    int block_y;    /*   block_y = 16, block_z = 8, both L when L <= 16); see ising_scheme */
+    int block_z;
 } ising_opts;
 
 /* Method of the correlation sums (identical results).  POPCOUNT: XOR + bit counts over
@@ -99,6 +103,27 @@ typedef enum { ISING_CORR_AUTO = 0, ISING_CORR_POPCOUNT = 1, ISING_CORR_TENSOR =
  * replicas > 1 each replica draws its own order (one launch per replica and half-sweep).
  * The batched form supports the 01 cycle only. */
 typedef enum { ISING_CYCLE_01 = 0, ISING_CYCLE_MIXED = 1 } ising_cycle;
+
+/* Update scheme of a sweep.  CHECKERBOARD: the two half-sweeps of the main text (Methods).
+ * DOUBLE: the double-checkerboard decomposition (Supp. Methods I A, Weigel's GPU scheme in
+ * d = 3).  The lattice is cut into blocks of block_x * block_y * block_z sites; block
+ * (i, j, k) = (x / block_x, y / block_y, z / block_z) is red when i + j + k is even.  A
+ * sweep updates all red blocks, then all blue ones; inside a block the sites of odd
+ * parity (x + y + z) first, then the even ones (the step list's "darker" sites first).
+ * With ISING_CYCLE_MIXED (Supp. Methods I B) the colour order is drawn per sweep and
+ * replica as for the checkerboard, and the parity each block starts with per block and
+ * sweep: block beta = i + nbx*(j + nby*k) starts with parity 1 when bit (beta & 31) of
+ * word ((beta >> 5) & 3) of Philox(counter (beta >> 7, t, 6, 0), key S) is 1.  A site's
+ * zero-energy decision uses the checkerboard's bit (phase = its parity), so 1x1x1 blocks
+ * give exactly the checkerboard sweep.  Requirements (else ISING_EINVAL at creation):
+ * PACKED form; block_y and block_z divide L with an even quotient (or equal L); block_x
+ * equals L, or (L >= 128) is a multiple of 64 dividing L with an even quotient; a block
+ * with a one-row halo on each side must fit in 227 KB of shared memory,
+ * 8 * (block_y + 2) * (block_z + 2) * (row words) bytes with row words = L/64 (1 for
+ * L < 64) when block_x = L, else block_x/64 + 8 when block_x is a multiple of 256 and
+ * block_x/64 + 2 otherwise.
+ * Not available in the batched form. */
+typedef enum { ISING_SCHEME_CHECKERBOARD = 0, ISING_SCHEME_DOUBLE = 1 } ising_scheme;
 
 /* Fill *opts with the defaults: GLAUBER, PACKED, own stream, current device, auto. */
 void ising_default_opts(ising_opts *opts);

@@ -317,7 +317,9 @@ int ising_batch_create(ising_batch **out, int nclass, const int *L, const int *r
     ising_opts o;
     ising_default_opts(&o);
     if (opts) o = *opts;
-    if (o.tie < 0 || o.tie > 2 || o.form != ISING_FORM_PACKED || o.cycle != ISING_CYCLE_01) return ISING_EINVAL;
+    if (o.tie < 0 || o.tie > 2 || o.form != ISING_FORM_PACKED || o.cycle != ISING_CYCLE_01 ||
+        o.scheme != ISING_SCHEME_CHECKERBOARD)
+        return ISING_EINVAL;
     for (int c = 0; c < nclass; ++c)
         if (!packed_L_ok(L[c]) || L[c] > 4096 || replicas[c] < 1 || replicas[c] > 65535) return ISING_EINVAL;
     ising_batch *b = new (std::nothrow) ising_batch();

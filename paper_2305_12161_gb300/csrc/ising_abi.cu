@@ -31,6 +31,7 @@ struct ising_ctx {
     int poisoned = 0;
     int64_t launches = 0;
     SweepConfig cfg{};
+    DcbGeom dcb{};  // double-checkerboard blocks (scheme DOUBLE)
     char err[256] = {0};
 };
 
@@ -102,6 +103,10 @@ void ising_default_opts(ising_opts *o)
     o->depth = 0;
     o->cycle = 0;
     o->corr = 0;
+    o->scheme = ISING_SCHEME_CHECKERBOARD;
+    o->block_x = 0;
+    o->block_y = 0;
+    o->block_z = 0;
 }
 
 int64_t ising_record_len(int L)
@@ -178,6 +183,11 @@ int ising_create_ex(ising_ctx **out, int L, int R, uint64_t seed, const ising_op
     // the measurement kernels always run on the packed store
     if (!packed_L_ok(L)) return ISING_EINVAL;
     if ((int64_t)L > 4096) return ISING_EINVAL;  // 32-bit Philox group index bound
+    DcbGeom dcb{};
+    if (o.scheme != ISING_SCHEME_CHECKERBOARD && o.scheme != ISING_SCHEME_DOUBLE) return ISING_EINVAL;
+    if (o.scheme == ISING_SCHEME_DOUBLE &&
+        (o.form != ISING_FORM_PACKED || !make_dcb_geom(L, o.block_x, o.block_y, o.block_z, &dcb)))
+        return ISING_EINVAL;
     ising_ctx *c = new (std::nothrow) ising_ctx();
     if (!c) return ISING_ENOMEM;
     c->L = L;
@@ -185,6 +195,7 @@ int ising_create_ex(ising_ctx **out, int L, int R, uint64_t seed, const ising_op
     c->seed = seed;
     c->opts = o;
     c->g = make_geom(L);
+    c->dcb = dcb;
     int dev = o.device;
     if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) {
         delete c;
@@ -292,7 +303,10 @@ int ising_sweep(ising_ctx *c, int64_t n)
     if (n == 0) return ISING_OK;
     DeviceGuard dg(c->device);
     cudaError_t e;
-    if (c->opts.form == ISING_FORM_PLAIN)
+    if (c->opts.scheme == ISING_SCHEME_DOUBLE)
+        e = launch_sweeps_dcb(c->lat, c->L, c->R, c->seed, c->opts.tie, c->t, n, c->opts.cycle, c->dcb, c->stream,
+                              &c->launches);
+    else if (c->opts.form == ISING_FORM_PLAIN)
         e = launch_sweeps_plain(c->plain, c->L, c->R, c->seed, c->opts.tie, c->t, n, c->opts.cycle, c->stream,
                                 &c->launches);
     else
@@ -475,7 +489,7 @@ int ising_tune_sweep(int L, int replicas, int probe_mcs, const ising_opts *base,
     ising_opts o;
     ising_default_opts(&o);
     if (base) o = *base;
-    if (o.form != ISING_FORM_PACKED) return ISING_EINVAL;
+    if (o.form != ISING_FORM_PACKED || o.scheme != ISING_SCHEME_CHECKERBOARD) return ISING_EINVAL;
     std::vector<SweepConfig> cands;
     cands.push_back(SweepConfig{VARIANT_WORD, 0, 0, 0});
     const int tzs[] = {4, 8, 16, 32, 64};

@@ -145,8 +145,10 @@ __device__ __forceinline__ void load_panel_yz(const uint32_t *S0, const uint32_t
     }
 }
 
+// Three CTAs per SM (80 registers): with that bound the compiler keeps the carry-save
+// registers without spilling; two CTAs with more registers measured 3% slower.
 template <int NT, int RT>
-__global__ void __launch_bounds__(NT) k_corr(const uint32_t *lat, Geom g, int64_t *rec)
+__global__ void __launch_bounds__(NT, 3) k_corr(const uint32_t *lat, Geom g, int64_t *rec)
 {
     extern __shared__ uint32_t csm[];
     const int axis = blockIdx.z;

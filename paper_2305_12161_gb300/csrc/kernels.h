@@ -41,6 +41,31 @@ int mixed_first(uint64_t S, uint32_t t);
 // Menger-sponge start of iteration k for every replica (padding words must be zero).
 cudaError_t launch_init_menger(uint32_t *lat, int L, int R, uint64_t seed, int k, cudaStream_t s);
 
+// Double-checkerboard update (Supp. Methods I A): blocks of bx*by*bz sites, red blocks
+// (block indices summing to an even number) then blue ones; inside a block the sites of one
+// parity, then the other.  A block row is the block's x-range of one row (y,z) of one
+// sublattice: m words, plus one halo word on each side when the block does not span x.
+struct DcbGeom {
+    int bx, by, bz;     // block sides in sites
+    int nbx, nby, nbz;  // blocks per axis (each even, or 1)
+    int m;              // words per block row and sublattice
+    int xh;             // 1: block rows carry x-halo words (bx < L)
+    int v;              // words per thread: 4 when m is a multiple of 4, else 1
+    int off, rs;        // offset of the block's own words and stride of a row in shared memory
+    int64_t nblk;       // blocks in the lattice
+};
+// Fill *d for an L^3 packed lattice (bx = 0: L; by = 0: 16, bz = 0: 8; both L when L <= 16).  False
+// when the tiling is not a double checkerboard the kernel supports: bx must be L or a
+// multiple of 64 with an even number of blocks, by and bz divisors of L with an even
+// quotient (or L), and a block with its halo must fit in 227 KB of shared memory.
+bool make_dcb_geom(int L, int bx, int by, int bz, DcbGeom *d);
+size_t dcb_smem_bytes(const DcbGeom &d);
+// n_mcs double-checkerboard sweeps from t0.  cycle 0: red blocks first, odd sites first in
+// every block; cycle 1: colour order per sweep and replica from mixed_first, fine order per
+// block from Philox phase 6.
+cudaError_t launch_sweeps_dcb(uint32_t *lat, int L, int R, uint64_t seed, int rule, int64_t t0, int64_t n_mcs,
+                              int cycle, const DcbGeom &d, cudaStream_t s, int64_t *launches);
+
 // ---- plain form: one byte per spin, replica r at plain + r*N. --------------------
 cudaError_t launch_init_plain(int8_t *plain, int L, int R, uint64_t seed, cudaStream_t s);
 cudaError_t launch_sweeps_plain(int8_t *plain, int L, int R, uint64_t seed, int rule, int64_t t0,

@@ -28,6 +28,7 @@ MEAS_DEVICE, MEAS_CONNECTED, MEAS_NO_CORR = 1, 2, 4
 PTR_DEVICE = 1
 CYCLE_01, CYCLE_MIXED = 0, 1
 CORR_AUTO, CORR_POPCOUNT, CORR_TENSOR = 0, 1, 2
+SCHEME_CHECKERBOARD, SCHEME_DOUBLE = 0, 1
 VARIANT_AUTO, VARIANT_WORD, VARIANT_ZMARCH, VARIANT_ZFAST, VARIANT_ZDEEP = 0, 1, 2, 3, 4
 
 
@@ -43,7 +44,9 @@ class IsingError(RuntimeError):
 class ising_opts(ctypes.Structure):
     _fields_ = [("tie", ctypes.c_int), ("form", ctypes.c_int), ("stream", ctypes.c_void_p),
                 ("device", ctypes.c_int), ("variant", ctypes.c_int), ("tile_y", ctypes.c_int),
-                ("tile_z", ctypes.c_int), ("depth", ctypes.c_int), ("cycle", ctypes.c_int), ("corr", ctypes.c_int)]
+                ("tile_z", ctypes.c_int), ("depth", ctypes.c_int), ("cycle", ctypes.c_int), ("corr", ctypes.c_int),
+                ("scheme", ctypes.c_int), ("block_x", ctypes.c_int), ("block_y", ctypes.c_int),
+                ("block_z", ctypes.c_int)]
 
 
 def lib_path() -> str:
@@ -163,13 +166,16 @@ class Ising:
 
     def __init__(self, L: int, replicas: int = 1, seed: int = 1, tie: int = TIE_GLAUBER, form: int = FORM_PACKED,
                  stream=None, device: int = -1, variant: int = 0, tile_y: int = 0, tile_z: int = 0, depth: int = 0,
-                 cycle: int = CYCLE_01, corr: int = CORR_AUTO):
+                 cycle: int = CYCLE_01, corr: int = CORR_AUTO, scheme: int = SCHEME_CHECKERBOARD,
+                 block=(0, 0, 0)):
         self._h = ctypes.c_void_p()
         o = ising_opts()
         lib().ising_default_opts(ctypes.byref(o))
         o.tie, o.form, o.device, o.variant, o.tile_y, o.tile_z, o.depth = tie, form, device, variant, tile_y, tile_z, depth
         o.cycle = cycle
         o.corr = corr
+        o.scheme = scheme
+        o.block_x, o.block_y, o.block_z = block
         sh = _stream_handle(stream)
         o.stream = sh if sh else None
         self._stream_obj = stream  # keep the caller's stream alive
