@@ -290,7 +290,7 @@ def run_dcb_case(args):
         "ms_per_mcs": ms / mcs, "launches": launches,
         "roofline": {"kernel": "k_sweep_dcb_rows (one colour)", "bound": "hbm", "achieved": achieved,
                      "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
-                     # DRAM bytes of one launch in one ncu capture (L=2048, 16 x 8 blocks, sweep t=2)
+                     # DRAM bytes of one launch in one ncu capture (L=2048, 16 x 8 blocks, sweep t=1)
                      "traffic": 1.2026e9 if (L, by, bz) == (2048, 16, 8) else None,
                      "avg_launch_ms": per_launch_s * 1e3, "bytes_per_launch": bytes_launch},
         "checkerboard_updates_per_ns": mcs * N / (ms_cb * 1e-3) / 1e9, "checkerboard_ms_per_mcs": ms_cb / mcs,
