@@ -97,6 +97,20 @@ def lib() -> ctypes.CDLL:
             L.orc_sweeps_dcb.argtypes = [ctypes.c_int, i8p, ctypes.c_uint32, ctypes.c_int64, ctypes.c_uint64,
                                          ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
             L.orc_sweeps_dcb.restype = ctypes.c_int
+            L.orc_isqrt.argtypes = [ctypes.c_int64]
+            L.orc_isqrt.restype = ctypes.c_int64
+            L.orc_radial_bin.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64]
+            L.orc_radial_bin.restype = ctypes.c_int64
+            L.orc_radial_nbins.argtypes = [ctypes.c_int]
+            L.orc_radial_nbins.restype = ctypes.c_int64
+            L.orc_corr3d.argtypes = [ctypes.c_int, i8p, i64p]
+            L.orc_corr3d.restype = None
+            L.orc_radial_corr.argtypes = [ctypes.c_int, i8p, f64p, i64p]
+            L.orc_radial_corr.restype = None
+            L.orc_structure_factor.argtypes = [ctypes.c_int, i8p, f64p, i64p]
+            L.orc_structure_factor.restype = None
+            L.orc_radial_length.argtypes = [ctypes.c_int, f64p, ctypes.c_double, ctypes.c_double]
+            L.orc_radial_length.restype = ctypes.c_double
             L.orc_derived.argtypes = [ctypes.c_int, i64p, ctypes.c_double, ctypes.c_int, f64p]
             L.orc_derived.restype = None
             _lib = L
@@ -199,6 +213,53 @@ def sweeps_dcb(s: np.ndarray, t0: int, n: int, S: int, block, rule: int = TIE_GL
     bx, by, bz = block
     if lib().orc_sweeps_dcb(L, _p(s, ctypes.c_int8), t0, n, S % 2**64, rule, bx, by, bz, int(bool(mixed))) != 0:
         raise ValueError(f"blocks {block} do not tile L={L} as a double checkerboard")
+
+
+def isqrt(n: int) -> int:
+    return int(lib().orc_isqrt(n))
+
+
+def radial_bin(L: int, x: int, y: int, z: int) -> int:
+    """Radial bin round(|v|) of the lag or mode vector with indices (x, y, z) (minimal images)."""
+    return int(lib().orc_radial_bin(L, x, y, z))
+
+
+def radial_nbins(L: int) -> int:
+    return int(lib().orc_radial_nbins(L))
+
+
+def corr3d(s: np.ndarray) -> np.ndarray:
+    """G(k) = sum_i s_i s_(i+k) for every lag, int64 array [kz, ky, kx] (brute force)."""
+    L = _check_lattice(s)
+    G = np.empty((L, L, L), dtype=np.int64)
+    lib().orc_corr3d(L, _p(s, ctypes.c_int8), _p(G, ctypes.c_int64))
+    return G
+
+
+def radial_corr(s: np.ndarray):
+    """(C(r), n_r): radially averaged G(k)/N and the number of lag vectors per bin."""
+    L = _check_lattice(s)
+    nb = radial_nbins(L)
+    C = np.empty(nb, dtype=np.float64)
+    n = np.empty(nb, dtype=np.int64)
+    lib().orc_radial_corr(L, _p(s, ctypes.c_int8), _p(C, ctypes.c_double), _p(n, ctypes.c_int64))
+    return C, n
+
+
+def structure_factor(s: np.ndarray):
+    """(S(b), n_b): radially averaged |DFT(s)|^2 / N by the direct sum, and modes per bin."""
+    L = _check_lattice(s)
+    nb = radial_nbins(L)
+    S = np.empty(nb, dtype=np.float64)
+    n = np.empty(nb, dtype=np.int64)
+    lib().orc_structure_factor(L, _p(s, ctypes.c_int8), _p(S, ctypes.c_double), _p(n, ctypes.c_int64))
+    return S, n
+
+
+def radial_length(L: int, C: np.ndarray, c: float = 0.5, sub: float = 0.0) -> float:
+    """Crossing of the radial C(r) with c for r <= L/2 (linear interpolation; NaN if none)."""
+    C = np.ascontiguousarray(C, dtype=np.float64)
+    return float(lib().orc_radial_length(L, _p(C, ctypes.c_double), c, sub))
 
 
 def record_len(L: int) -> int:

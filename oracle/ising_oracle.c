@@ -462,3 +462,149 @@ int orc_sweeps_dcb(int L_, int8_t *s, uint32_t t0, int64_t n, uint64_t S, int ru
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------------------ */
+/* Three-dimensional correlation and structure factor, radially averaged (Methods,
+ * "Calculating the correlation function": the paper obtains the spin-spin sum for every
+ * lag vector from an FFT, Eq. (3), and averages it radially; Results: S(k,t) is the
+ * Fourier transform of C).  Written out here from the definitions, by brute force.
+ *
+ * Lag and mode vectors: each component j in [0, L) stands for its minimal image
+ * d = j for j <= L/2, j - L otherwise (|d| = L/2 for j = L/2 either way).
+ * Radial bin of a vector with squared length D: b = round(sqrt(D)), computed exactly in
+ * integers as (isqrt(4D) + 1) / 2 (sqrt(D) + 1/2 is never an integer for integer D, so no
+ * vector sits on a bin edge).  Bins b = 0 .. nbins-1, nbins = (isqrt(3 L^2) + 1)/2 + 1;
+ * bins beyond L/2 are cut by the cube's corners. */
+int64_t orc_isqrt(int64_t n)
+{
+    if (n <= 0) return 0;
+    int64_t lo = 0, hi = 1;
+    while (hi * hi <= n) hi *= 2;
+    while (hi - lo > 1) {  /* invariant: lo^2 <= n < hi^2 */
+        const int64_t mid = lo + (hi - lo) / 2;
+        if (mid * mid <= n) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+static inline int64_t min_image(int64_t j, int64_t L) { return j <= L / 2 ? j : j - L; }
+
+int64_t orc_radial_bin(int L_, int64_t x, int64_t y, int64_t z)
+{
+    const int64_t L = L_;
+    const int64_t a = min_image(x, L), b = min_image(y, L), c = min_image(z, L);
+    return (orc_isqrt(4 * (a * a + b * b + c * c)) + 1) / 2;
+}
+
+int64_t orc_radial_nbins(int L_)
+{
+    const int64_t L = L_;
+    return (orc_isqrt(3 * L * L) + 1) / 2 + 1;
+}
+
+/* G(k) = sum_i s_i s_(i+k) for every lag k = (kx, ky, kz), stored at kx + L(ky + L kz):
+ * the double sum of Eq. (2) over all pairs at that separation, O(N^2). */
+void orc_corr3d(int L_, const int8_t *s, int64_t *G)
+{
+    const int64_t L = L_;
+    const int64_t N = L * L * L;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t k = 0; k < N; ++k) {
+        const int64_t kx = k % L, ky = (k / L) % L, kz = k / (L * L);
+        int64_t acc = 0;
+        for (int64_t z = 0; z < L; ++z)
+            for (int64_t y = 0; y < L; ++y)
+                for (int64_t x = 0; x < L; ++x)
+                    acc += (int64_t)s[site(L, x, y, z)] *
+                           (int64_t)s[site(L, (x + kx) % L, (y + ky) % L, (z + kz) % L)];
+        G[k] = acc;
+    }
+}
+
+/* Radially averaged correlation C(r) = (1/n_r) sum_{k in bin r} G(k)/N and the number n_r
+ * of lag vectors in each bin. */
+void orc_radial_corr(int L_, const int8_t *s, double *C, int64_t *count)
+{
+    const int64_t L = L_;
+    const int64_t N = L * L * L;
+    const int64_t nb = orc_radial_nbins(L_);
+    int64_t *G = (int64_t *)malloc(sizeof(int64_t) * (size_t)N);
+    if (!G) return;
+    orc_corr3d(L_, s, G);
+    for (int64_t b = 0; b < nb; ++b) {
+        C[b] = 0.0;
+        count[b] = 0;
+    }
+    for (int64_t k = 0; k < N; ++k) {
+        const int64_t b = orc_radial_bin(L_, k % L, (k / L) % L, k / (L * L));
+        C[b] += (double)G[k] / (double)N;
+        count[b] += 1;
+    }
+    for (int64_t b = 0; b < nb; ++b)
+        if (count[b]) C[b] /= (double)count[b];
+    free(G);
+}
+
+/* Structure factor S(n) = |sum_x s_x exp(-2 pi i n.x / L)|^2 / N for every mode
+ * n = (nx, ny, nz) (wave vector 2 pi n / L), by the direct O(N^2) sum, radially averaged
+ * over the same bins as C (bin b is wave number 2 pi b / L).  The phase n.x mod L indexes a
+ * table of the L complex roots of unity. */
+void orc_structure_factor(int L_, const int8_t *s, double *S, int64_t *count)
+{
+    const int64_t L = L_;
+    const int64_t N = L * L * L;
+    const int64_t nb = orc_radial_nbins(L_);
+    double *cs = (double *)malloc(sizeof(double) * 2 * (size_t)L);
+    double *P = (double *)malloc(sizeof(double) * (size_t)N);
+    if (!cs || !P) {
+        free(cs);
+        free(P);
+        return;
+    }
+    for (int64_t j = 0; j < L; ++j) {
+        const double two_pi = 6.283185307179586476925286766559;
+        cs[2 * j] = cos(two_pi * (double)j / (double)L);
+        cs[2 * j + 1] = -sin(two_pi * (double)j / (double)L);
+    }
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t n = 0; n < N; ++n) {
+        const int64_t nx = n % L, ny = (n / L) % L, nz = n / (L * L);
+        double re = 0.0, im = 0.0;
+        for (int64_t z = 0; z < L; ++z)
+            for (int64_t y = 0; y < L; ++y)
+                for (int64_t x = 0; x < L; ++x) {
+                    const int64_t ph = (nx * x + ny * y + nz * z) % L;
+                    const double v = (double)s[site(L, x, y, z)];
+                    re += v * cs[2 * ph];
+                    im += v * cs[2 * ph + 1];
+                }
+        P[n] = (re * re + im * im) / (double)N;
+    }
+    for (int64_t b = 0; b < nb; ++b) {
+        S[b] = 0.0;
+        count[b] = 0;
+    }
+    for (int64_t n = 0; n < N; ++n) {
+        const int64_t b = orc_radial_bin(L_, n % L, (n / L) % L, n / (L * L));
+        S[b] += P[n];
+        count[b] += 1;
+    }
+    for (int64_t b = 0; b < nb; ++b)
+        if (count[b]) S[b] /= (double)count[b];
+    free(cs);
+    free(P);
+}
+
+/* Length from the radial C: the crossing rule of orc_derived applied to C(r) for
+ * r = 0 .. L/2 (the shells that the cube contains whole): r0 + (C(r0) - c)/(C(r0) - C(r0+1))
+ * at the first r0 < L/2 with C(r0) >= c > C(r0+1), NaN if none; `sub` is subtracted from C
+ * first (m^2 for the connected variant). */
+double orc_radial_length(int L_, const double *C, double c, double sub)
+{
+    const int64_t R = L_ / 2;
+    for (int64_t r = 0; r < R; ++r) {
+        const double c0 = C[r] - sub, c1 = C[r + 1] - sub;
+        if (c0 >= c && c > c1) return (double)r + (c0 - c) / (c0 - c1);
+    }
+    return NAN;
+}
