@@ -522,27 +522,32 @@ void orc_corr3d(int L_, const int8_t *s, int64_t *G)
 }
 
 /* Radially averaged correlation C(r) = (1/n_r) sum_{k in bin r} G(k)/N and the number n_r
- * of lag vectors in each bin. */
+ * of lag vectors in each bin.  The integer sums of G over a bin are formed first and
+ * divided once, C(r) = (double) sum_G / ((double) N * (double) n_r), so the value does not
+ * depend on the order of summation. */
 void orc_radial_corr(int L_, const int8_t *s, double *C, int64_t *count)
 {
     const int64_t L = L_;
     const int64_t N = L * L * L;
     const int64_t nb = orc_radial_nbins(L_);
     int64_t *G = (int64_t *)malloc(sizeof(int64_t) * (size_t)N);
-    if (!G) return;
-    orc_corr3d(L_, s, G);
-    for (int64_t b = 0; b < nb; ++b) {
-        C[b] = 0.0;
-        count[b] = 0;
+    int64_t *sumG = (int64_t *)calloc((size_t)nb, sizeof(int64_t));
+    if (!G || !sumG) {
+        free(G);
+        free(sumG);
+        return;
     }
+    orc_corr3d(L_, s, G);
+    for (int64_t b = 0; b < nb; ++b) count[b] = 0;
     for (int64_t k = 0; k < N; ++k) {
         const int64_t b = orc_radial_bin(L_, k % L, (k / L) % L, k / (L * L));
-        C[b] += (double)G[k] / (double)N;
+        sumG[b] += G[k];
         count[b] += 1;
     }
     for (int64_t b = 0; b < nb; ++b)
-        if (count[b]) C[b] /= (double)count[b];
+        C[b] = count[b] ? (double)sumG[b] / ((double)N * (double)count[b]) : 0.0;
     free(G);
+    free(sumG);
 }
 
 /* Structure factor S(n) = |sum_x s_x exp(-2 pi i n.x / L)|^2 / N for every mode
