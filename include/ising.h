@@ -154,6 +154,33 @@ int ising_init_menger(ising_ctx *ctx, int k);
  * time t by n_mcs.  Returns once the work is enqueued. */
 int ising_sweep(ising_ctx *ctx, int64_t n_mcs);
 
+/* ---- Radially averaged three-dimensional correlation and structure factor ----------
+ * (Methods, "Calculating the correlation function": the spin-spin sum over every lag
+ * vector k, G(k) = sum_i s_i s_(i+k), from two FFTs, Eq. (3), then averaged radially;
+ * Results: the structure factor S(k,t), the Fourier transform of C.)
+ * Lag and mode components are minimal images (j <= L/2: j, else j - L); a vector of squared
+ * length D falls in bin b = round(sqrt(D)) = (isqrt(4D) + 1) / 2, b = 0 .. nbins-1 with
+ * nbins = ising_radial_bins(L) = round(sqrt(3) L / 2) + 1; bins beyond L/2 are cut by the
+ * cube's corners.
+ *   C[b] = (sum of G(k) over the bin's lags) / (N * count[b])
+ *   S[b] = (sum of |FFT(s)(q)|^2 over the bin's modes) / (N * count[b]), wave number 2 pi b / L
+ *   *ell = the radial C's first downward crossing of cval for r <= L/2, linearly
+ *          interpolated (NaN if none)
+ * count[b] is the number of lag (= mode) vectors in the bin.  precision: ISING_FFT_SINGLE
+ * (fp32 cuFFT, C and S within the rounding error of single-precision FFTs) or
+ * ISING_FFT_DOUBLE (fp64: G(k) is rounded to its exact integer, so C is exact; *inexact
+ * receives the number of lags whose FFT value lay more than 1/4 from an integer, 0 when C is
+ * exact; -1 in single precision).  Host outputs: C and S of nbins doubles (required), count
+ * of nbins int64, ell, inexact (each may be NULL).  Replica `replica` only.  Allocates, in
+ * stream order, L^2 (L/2+1) complex values of the chosen precision (34.4 GB at L=2048 in
+ * single precision, twice that in double) plus cuFFT's work area, and frees them before
+ * returning; ISING_ENOMEM (context still usable) if the device has no room.  Synchronises
+ * the context's stream.  Returns -1 from ising_radial_bins for a bad L. */
+typedef enum { ISING_FFT_SINGLE = 0, ISING_FFT_DOUBLE = 1 } ising_fft_precision;
+int64_t ising_radial_bins(int L);
+int ising_measure_radial(ising_ctx *ctx, int replica, int precision, double cval, double *C, double *S,
+                         int64_t *count, double *ell, int64_t *inexact);
+
 /* Number of int64 values of one replica's record:
  *   [t, M, B, D_x(0..L/2), D_y(0..L/2), D_z(0..L/2)]  -> 3 + 3*(L/2 + 1),
  * t = completed MCS, M = sum_i s_i, B = number of unequal nearest-neighbour pairs

@@ -105,6 +105,8 @@ def lib() -> ctypes.CDLL:
             L.orc_radial_nbins.restype = ctypes.c_int64
             L.orc_corr3d.argtypes = [ctypes.c_int, i8p, i64p]
             L.orc_corr3d.restype = None
+            L.orc_corr_vec.argtypes = [ctypes.c_int, i8p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64]
+            L.orc_corr_vec.restype = ctypes.c_int64
             L.orc_radial_corr.argtypes = [ctypes.c_int, i8p, f64p, i64p]
             L.orc_radial_corr.restype = None
             L.orc_structure_factor.argtypes = [ctypes.c_int, i8p, f64p, i64p]
@@ -234,6 +236,12 @@ def corr3d(s: np.ndarray) -> np.ndarray:
     G = np.empty((L, L, L), dtype=np.int64)
     lib().orc_corr3d(L, _p(s, ctypes.c_int8), _p(G, ctypes.c_int64))
     return G
+
+
+def corr_vec(s: np.ndarray, dx: int, dy: int, dz: int) -> int:
+    """G(k) = sum_i s_i s_(i+k) for one lag vector k = (dx, dy, dz)."""
+    L = _check_lattice(s)
+    return int(lib().orc_corr_vec(L, _p(s, ctypes.c_int8), dx, dy, dz))
 
 
 def radial_corr(s: np.ndarray):

@@ -613,3 +613,21 @@ double orc_radial_length(int L_, const double *C, double c, double sub)
     }
     return NAN;
 }
+
+/* G(k) = sum_i s_i s_(i+k) for the single lag vector k = (dx, dy, dz) (any integers, taken
+ * modulo L): the same double sum as orc_corr3d for one k, so that lags can be checked at
+ * lattice sizes where the full O(N^2) array is out of reach. */
+int64_t orc_corr_vec(int L_, const int8_t *s, int64_t dx, int64_t dy, int64_t dz)
+{
+    const int64_t L = L_;
+    const int64_t ox = wrap(dx, L), oy = wrap(dy, L), oz = wrap(dz, L);
+    int64_t acc = 0;
+#pragma omp parallel for schedule(static) reduction(+ : acc)
+    for (int64_t z = 0; z < L; ++z)
+        for (int64_t y = 0; y < L; ++y) {
+            const int8_t *a = s + site(L, 0, y, z);
+            const int8_t *b = s + site(L, 0, (y + oy) % L, (z + oz) % L);
+            for (int64_t x = 0; x < L; ++x) acc += (int64_t)a[x] * (int64_t)b[(x + ox) % L];
+        }
+    return acc;
+}

@@ -1,8 +1,9 @@
 """Build ``libising.so`` (the C-ABI library) in-tree with nvcc for sm_103a.
 
 Each ``csrc/*.cu`` translation unit is compiled in parallel, then linked into one
-shared library with the CUDA runtime linked statically, so the library depends on the
-driver only.  Re-running is cheap: objects newer than their sources and headers are
+shared library with the CUDA runtime linked statically; the only other CUDA library it
+loads is cuFFT (the FFT step of the radial correlation), found through an rpath to the
+toolkit's library directory.  Re-running is cheap: objects newer than their sources and headers are
 reused.
 """
 from __future__ import annotations
@@ -74,7 +75,9 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
                     raise RuntimeError("nvcc failed: " + " ".join(cmd))
     if force or jobs or _stale(LIB, objs):
         tmp = LIB + ".tmp"
-        cmd = [cc, *ARCH, "-shared", "-cudart", "static", *objs, "-o", tmp]
+        cudalib = os.path.realpath(os.path.join(os.path.dirname(os.path.realpath(cc)), "..", "lib64"))
+        cmd = [cc, *ARCH, "-shared", "-cudart", "static", *objs, "-o", tmp, "-lcufft",
+               "-Xlinker", "-rpath", "-Xlinker", cudalib]
         p = subprocess.run(cmd, capture_output=True, text=True)
         if p.returncode != 0:
             sys.stderr.write(p.stdout + p.stderr)

@@ -11,6 +11,7 @@
 #include "../../include/ising.h"
 #include "common.cuh"
 #include "kernels.h"
+#include <cufft.h>
 
 using namespace ising;
 
@@ -32,6 +33,7 @@ struct ising_ctx {
     int64_t launches = 0;
     SweepConfig cfg{};
     DcbGeom dcb{};  // double-checkerboard blocks (scheme DOUBLE)
+    RadialPlans *radial = nullptr;  // cuFFT plans of the radial measurement (first use)
     char err[256] = {0};
 };
 
@@ -162,6 +164,7 @@ int ising_destroy(ising_ctx *c)
             if (c->xt) cudaFreeAsync(c->xt, c->stream);
             cudaStreamSynchronize(c->stream);
         }
+        radial_plans_destroy(c->radial);
         if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     }
     delete c;
@@ -314,6 +317,64 @@ int ising_sweep(ising_ctx *c, int64_t n)
                                  &c->launches);
     if (e != cudaSuccess) return cuda_fail(c, e, "sweep launch");
     c->t += n;
+    return ISING_OK;
+}
+
+int64_t ising_radial_bins(int L)
+{
+    if (L < 4 || L % 2 != 0 || L > 4096) return -1;
+    return radial_nbins(L);
+}
+
+int ising_measure_radial(ising_ctx *c, int replica, int precision, double cval, double *C, double *S, int64_t *count,
+                         double *ell, int64_t *inexact)
+{
+    int s = check_ctx(c);
+    if (s) return s;
+    if (replica < 0 || replica >= c->R) return fail(c, ISING_EINVAL, "replica out of range");
+    if (precision != ISING_FFT_SINGLE && precision != ISING_FFT_DOUBLE) return fail(c, ISING_EINVAL, "precision");
+    if (!C || !S) return fail(c, ISING_EINVAL, "null output");
+    DeviceGuard dg(c->device);
+    if (!c->radial && !(c->radial = radial_plans_create())) return fail(c, ISING_ENOMEM, "radial plans");
+    if (c->opts.form == ISING_FORM_PLAIN) {
+        CK(c, launch_pack(c->plain, c->lat, c->L, c->R, c->stream));
+        c->launches += 1;
+    }
+    const int64_t nb = radial_nbins(c->L);
+    double *out = nullptr;
+    int64_t *cnt = nullptr;
+    if (cudaMallocAsync((void **)&out, sizeof(double) * (size_t)(2 * nb + 1), c->stream) != cudaSuccess)
+        return fail(c, ISING_ENOMEM, "radial output");
+    if (cudaMallocAsync((void **)&cnt, sizeof(int64_t) * (size_t)(nb + 1), c->stream) != cudaSuccess) {
+        cudaFreeAsync(out, c->stream);
+        return fail(c, ISING_ENOMEM, "radial output");
+    }
+    int cs = 0;
+    const uint32_t *lat_r = c->lat + 2 * (int64_t)replica * c->g.nw;
+    cudaError_t e = launch_radial(c->radial, lat_r, c->L, precision, cval, out, cnt, c->stream, &c->launches, &cs);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(cnt, c->stream);
+        cudaFreeAsync(out, c->stream);
+        if (e == cudaErrorMemoryAllocation || cs == CUFFT_ALLOC_FAILED) {
+            cudaGetLastError();  // a failed allocation is not sticky
+            return fail(c, ISING_ENOMEM, "radial measurement: scratch of %zu bytes",
+                        radial_scratch_bytes(c->L, precision));
+        }
+        if (cs) return fail(c, ISING_ECUDA, "cuFFT status %d", cs);
+        return cuda_fail(c, e, "radial measurement");
+    }
+    std::vector<double> h(2 * nb + 1);
+    std::vector<int64_t> hc(nb + 1);
+    CK(c, cudaMemcpyAsync(h.data(), out, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaMemcpyAsync(hc.data(), cnt, sizeof(int64_t) * hc.size(), cudaMemcpyDeviceToHost, c->stream));
+    cudaFreeAsync(cnt, c->stream);
+    cudaFreeAsync(out, c->stream);
+    CK(c, cudaStreamSynchronize(c->stream));
+    std::copy(h.begin(), h.begin() + nb, C);
+    std::copy(h.begin() + nb, h.begin() + 2 * nb, S);
+    if (ell) *ell = h[2 * nb];
+    if (count) std::copy(hc.begin(), hc.begin() + nb, count);
+    if (inexact) *inexact = hc[nb];
     return ISING_OK;
 }
 

@@ -66,6 +66,20 @@ size_t dcb_smem_bytes(const DcbGeom &d);
 cudaError_t launch_sweeps_dcb(uint32_t *lat, int L, int R, uint64_t seed, int rule, int64_t t0, int64_t n_mcs,
                               int cycle, const DcbGeom &d, cudaStream_t s, int64_t *launches);
 
+// Radially averaged 3-d correlation and structure factor of one lattice (lat_r: replica's
+// packed store) through cuFFT; precision 0: single, 1: double (exact integer G(k)).
+// out (device): [C(0..nb-1), S(0..nb-1), l]; cnt (device): [n_b (nb), inexact lags].
+// Allocates, stream-ordered, radial_scratch_bytes(L, precision) plus cuFFT's work area and
+// frees them before returning.  On a cuFFT failure returns cudaErrorUnknown with the cuFFT
+// status in *cufft_status.
+struct RadialPlans;
+RadialPlans *radial_plans_create();
+void radial_plans_destroy(RadialPlans *p);
+int64_t radial_nbins(int L);
+size_t radial_scratch_bytes(int L, int precision);
+cudaError_t launch_radial(RadialPlans *p, const uint32_t *lat_r, int L, int precision, double c, double *out,
+                          int64_t *cnt, cudaStream_t s, int64_t *launches, int *cufft_status);
+
 // ---- plain form: one byte per spin, replica r at plain + r*N. --------------------
 cudaError_t launch_init_plain(int8_t *plain, int L, int R, uint64_t seed, cudaStream_t s);
 cudaError_t launch_sweeps_plain(int8_t *plain, int L, int R, uint64_t seed, int rule, int64_t t0,

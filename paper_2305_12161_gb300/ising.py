@@ -29,6 +29,7 @@ PTR_DEVICE = 1
 CYCLE_01, CYCLE_MIXED = 0, 1
 CORR_AUTO, CORR_POPCOUNT, CORR_TENSOR = 0, 1, 2
 SCHEME_CHECKERBOARD, SCHEME_DOUBLE = 0, 1
+FFT_SINGLE, FFT_DOUBLE = 0, 1
 VARIANT_AUTO, VARIANT_WORD, VARIANT_ZMARCH, VARIANT_ZFAST, VARIANT_ZDEEP = 0, 1, 2, 3, 4
 
 
@@ -73,6 +74,9 @@ def lib() -> ctypes.CDLL:
                 "ising_record_len": (ctypes.c_int64, [ctypes.c_int]),
                 "ising_measure": (ctypes.c_int, [vp, vp]),
                 "ising_measure_ex": (ctypes.c_int, [vp, vp, vp, ctypes.c_double, ctypes.c_uint]),
+                "ising_radial_bins": (ctypes.c_int64, [ctypes.c_int]),
+                "ising_measure_radial": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, vp, vp,
+                                                        vp, vp, vp]),
                 "ising_get_spins": (ctypes.c_int, [vp, ctypes.c_int, vp]),
                 "ising_set_spins": (ctypes.c_int, [vp, ctypes.c_int, vp]),
                 "ising_packed_words": (ctypes.c_int64, [ctypes.c_int]),
@@ -151,6 +155,11 @@ def ising_record_len(L: int) -> int:
     return int(lib().ising_record_len(L))
 
 
+def ising_radial_bins(L: int) -> int:
+    """Number of radial bins round(sqrt(3) L/2) + 1 of the radial C and S (-1 for a bad L)."""
+    return int(lib().ising_radial_bins(L))
+
+
 def ising_packed_words(L: int) -> int:
     return int(lib().ising_packed_words(L))
 
@@ -224,6 +233,20 @@ class Ising:
         flags = (MEAS_CONNECTED if connected else 0) | (0 if corr else MEAS_NO_CORR)
         self._check(lib().ising_measure_ex(self._h, rec.ctypes.data, der.ctypes.data, c, flags), "ising_measure_ex")
         return rec, der
+
+    def measure_radial(self, replica: int = 0, precision: int = FFT_SINGLE, c: float = 0.5) -> dict:
+        """Radially averaged 3-d correlation C(b), structure factor S(b), vectors per bin,
+        the length at which C crosses c, and (double precision) the number of inexact lags."""
+        nb = ising_radial_bins(self.L)
+        C = np.empty(nb, dtype=np.float64)
+        S = np.empty(nb, dtype=np.float64)
+        n = np.empty(nb, dtype=np.int64)
+        ell = ctypes.c_double()
+        bad = ctypes.c_int64()
+        self._check(lib().ising_measure_radial(self._h, replica, precision, c, C.ctypes.data, S.ctypes.data,
+                                               n.ctypes.data, ctypes.addressof(ell), ctypes.addressof(bad)),
+                    "ising_measure_radial")
+        return {"C": C, "S": S, "count": n, "ell": ell.value, "inexact": bad.value}
 
     def measure_device(self, rec, derived=None, c: float = 0.5, connected: bool = False, corr: bool = True) -> None:
         """Enqueue a measurement into device buffers (no synchronisation)."""

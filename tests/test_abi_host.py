@@ -40,6 +40,15 @@ def test_record_and_packed_sizes(lib):
     assert ising.ising_packed_words(96) == -1  # packed form: multiples of 64 or 4..32
 
 
+def test_radial_bins_match_the_oracle(lib):
+    import oracle
+    from paper_2305_12161_gb300 import ising
+    for L in (4, 6, 8, 16, 32, 64, 256, 2048, 4096):
+        assert ising.ising_radial_bins(L) == oracle.radial_nbins(L), L
+    assert ising.ising_radial_bins(2048) == 1775
+    assert ising.ising_radial_bins(7) == -1 and ising.ising_radial_bins(2) == -1
+
+
 def test_strerror_and_variants(lib):
     from paper_2305_12161_gb300 import ising
     for code in range(0, -7, -1):

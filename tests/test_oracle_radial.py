@@ -11,6 +11,7 @@
 * Closed forms: uniform state (C = 1, S only at k = 0), Neel state (G = N (-1)^(kx+ky+kz),
   S only at the corner mode), flat stripes (triangle-wave G along the stripe normal).
 * The radial crossing rule on hand-made C arrays.
+* The single-lag G equals the full array's entry for every lag (negative components too).
 """
 import math
 
@@ -130,3 +131,14 @@ def test_radial_length_rule():
     assert oracle.radial_length(L, C, 0.8) == pytest.approx(1.0)  # C(1) >= c > C(2)
     assert math.isnan(oracle.radial_length(L, C, 0.01))  # crosses only beyond L/2
     assert oracle.radial_length(L, C, 0.3, sub=0.2) == pytest.approx(1.75)
+
+
+def test_corr_vec_matches_corr3d():
+    L = 8
+    s = oracle.init(L, 9)
+    G = oracle.corr3d(s)
+    for kz in range(L):
+        for ky in range(L):
+            for kx in range(L):
+                assert oracle.corr_vec(s, kx, ky, kz) == G[kz, ky, kx]
+    assert oracle.corr_vec(s, -1, 2, -3) == G[(-3) % L, 2, (-1) % L]
