@@ -297,6 +297,44 @@ def run_dcb_case(args):
         "clocks": clk}))
 
 
+def run_radial_case(args):
+    """The radially averaged 3-d correlation and structure factor (two cuFFT transforms and
+    the library's unpack / power / binning kernels) of one L^3 lattice after --mcs sweeps
+    from the T = inf start: one untimed call per precision, then --steps calls timed with
+    CUDA events around each (the call synchronises its stream)."""
+    import torch
+
+    import __graft_entry__
+    from paper_2305_12161_gb300 import ising
+    __graft_entry__.build()
+    L = args.L
+    stream = torch.cuda.Stream()
+    out = {"case": "radial", "metric": "ms per radial C(r) + S(k) measurement (Eq. 3, radial average), one GB300",
+           "unit": "ms", "higher_is_better": False,
+           "config": {"workload": f"L={L} single lattice after {args.mcs} MCS from the T=inf start",
+                      "L": L, "steps": args.steps}}
+    clocks = ClockSampler(0)
+    clocks.start()
+    with ising.Ising(L, seed=1, stream=stream) as q:
+        q.sweep(args.mcs)
+        for prec, name in ((ising.FFT_SINGLE, "fp32"), (ising.FFT_DOUBLE, "fp64")):
+            r = q.measure_radial(precision=prec)
+            ms = []
+            for _ in range(args.steps):
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                r = q.measure_radial(precision=prec)
+                b.record(stream)
+                b.synchronize()
+                ms.append(a.elapsed_time(b))
+            out[name] = {"ms": statistics.median(ms), "ell": r["ell"], "inexact": r["inexact"],
+                         "C_1_to_4": [float(v) for v in r["C"][1:5]]}
+    out["clocks"] = clocks.stop()
+    out["value"] = out["fp32"]["ms"]
+    print(json.dumps(out))
+
+
 def run_serve_case(args):
     """Continuous-batching serving on a finite seeded trace: Poisson arrivals at 20/s,
     L log-uniform on {64..1024}, t_max = 10^U[3,5] MCS, 1-16 replicas, 12 log-spaced
@@ -342,7 +380,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--block-y", type=int, default=16, help="dcb case: block rows along y")
     ap.add_argument("--block-z", type=int, default=8, help="dcb case: block planes along z")
-    ap.add_argument("--case", default="bench", choices=["bench", "quench", "serve", "batch", "dcb"],
+    ap.add_argument("--case", default="bench", choices=["bench", "quench", "serve", "batch", "dcb", "radial"],
                     help="quench: init + --mcs sweeps + one measurement, untimed (for profilers); "
                          "serve: the serving loop on the first --requests arrivals of the seeded trace")
     ap.add_argument("--requests", type=int, default=24)
@@ -361,6 +399,9 @@ def main():
         return
     if args.case == "dcb":
         run_dcb_case(args)
+        return
+    if args.case == "radial":
+        run_radial_case(args)
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

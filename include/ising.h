@@ -166,20 +166,27 @@ int ising_sweep(ising_ctx *ctx, int64_t n_mcs);
  *   S[b] = (sum of |FFT(s)(q)|^2 over the bin's modes) / (N * count[b]), wave number 2 pi b / L
  *   *ell = the radial C's first downward crossing of cval for r <= L/2, linearly
  *          interpolated (NaN if none)
- * count[b] is the number of lag (= mode) vectors in the bin.  precision: ISING_FFT_SINGLE
- * (fp32 cuFFT, C and S within the rounding error of single-precision FFTs) or
- * ISING_FFT_DOUBLE (fp64: G(k) is rounded to its exact integer, so C is exact; *inexact
- * receives the number of lags whose FFT value lay more than 1/4 from an integer, 0 when C is
- * exact; -1 in single precision).  Host outputs: C and S of nbins doubles (required), count
- * of nbins int64, ell, inexact (each may be NULL).  Replica `replica` only.  Allocates, in
- * stream order, L^2 (L/2+1) complex values of the chosen precision (34.4 GB at L=2048 in
- * single precision, twice that in double) plus cuFFT's work area, and frees them before
- * returning; ISING_ENOMEM (context still usable) if the device has no room.  Synchronises
- * the context's stream.  Returns -1 from ising_radial_bins for a bad L. */
+ * count[b] is the number of lag (= mode) vectors in the bin.  G(k) is an integer: the
+ * library rounds every FFT value g/N to the nearest integer before summing, so C is exact
+ * whenever the FFT error stays below 1/2; *inexact receives the number of lags whose value lay
+ * more than 1/4 from an integer (0: C is exact).  precision: ISING_FFT_SINGLE (fp32 cuFFT;
+ * exact at small L, within the rounding error of single-precision FFTs at large L) or
+ * ISING_FFT_DOUBLE (fp64 cuFFT: exact up to L = 2048 at least; S to fp64 rounding).  Host
+ * outputs: C and S of nbins doubles (required), count of nbins int64, ell, inexact (each may
+ * be NULL).  Replica `replica` only.  The first call allocates, in stream order,
+ * L^2 (L/2+1) complex values of the chosen precision (34.4 GB at L=2048 in single
+ * precision, twice that in double) plus cuFFT's work area, and keeps them in the context for
+ * later calls (ising_release_scratch frees them); ISING_ENOMEM (context still usable) if the
+ * device has no room.  Synchronises the context's stream.  ising_radial_bins returns -1 for a
+ * bad L. */
 typedef enum { ISING_FFT_SINGLE = 0, ISING_FFT_DOUBLE = 1 } ising_fft_precision;
 int64_t ising_radial_bins(int L);
 int ising_measure_radial(ising_ctx *ctx, int replica, int precision, double cval, double *C, double *S,
                          int64_t *count, double *ell, int64_t *inexact);
+/* Free the scratch that measurements keep in the context (the radial measurement's transform
+ * buffer and work area, the tensor-core correlation's transposed lattice); the next
+ * measurement that needs it allocates it again.  Synchronises the context's stream. */
+int ising_release_scratch(ising_ctx *ctx);
 
 /* Number of int64 values of one replica's record:
  *   [t, M, B, D_x(0..L/2), D_y(0..L/2), D_z(0..L/2)]  -> 3 + 3*(L/2 + 1),

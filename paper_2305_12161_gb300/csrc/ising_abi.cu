@@ -162,9 +162,10 @@ int ising_destroy(ising_ctx *c)
             if (c->rec_dev) cudaFreeAsync(c->rec_dev, c->stream);
             if (c->der_dev) cudaFreeAsync(c->der_dev, c->stream);
             if (c->xt) cudaFreeAsync(c->xt, c->stream);
+            radial_plans_destroy(c->radial, c->stream);
+            c->radial = nullptr;
             cudaStreamSynchronize(c->stream);
         }
-        radial_plans_destroy(c->radial);
         if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     }
     delete c;
@@ -375,6 +376,18 @@ int ising_measure_radial(ising_ctx *c, int replica, int precision, double cval, 
     if (ell) *ell = h[2 * nb];
     if (count) std::copy(hc.begin(), hc.begin() + nb, count);
     if (inexact) *inexact = hc[nb];
+    return ISING_OK;
+}
+
+int ising_release_scratch(ising_ctx *c)
+{
+    int s = check_ctx(c);
+    if (s) return s;
+    DeviceGuard dg(c->device);
+    radial_release(c->radial, c->stream);
+    if (c->xt) cudaFreeAsync(c->xt, c->stream);
+    c->xt = nullptr;
+    CK(c, cudaStreamSynchronize(c->stream));
     return ISING_OK;
 }
 

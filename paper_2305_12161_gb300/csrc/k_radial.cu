@@ -10,12 +10,18 @@
 //      (modes with 0 < qx < L/2 stand for their Hermitian partner too), and written back
 //      as (P, 0) for the inverse.
 //   4. cuFFT C2R: g(k) = sum_q P(q) e^{iqk} = N G(k), G(k) = sum_i s_i s_(i+k).
-//   5. k_radial_corr: G(k) = g/N summed per radial bin.  In double precision the FFT error
-//      is far below 1/2, so G is rounded to its exact integer and the bin sums are exact
-//      (every lag whose g/N lies more than 1/4 from an integer is counted as inexact); in
-//      single precision the bin sums are accumulated in double from the rounded-off values.
+//   5. k_radial_corr: G(k) = g/N rounded to the nearest integer and summed per radial bin in
+//      int64.  G(k) is an integer; when the FFT error stays below 1/2 (always in double
+//      precision, at small L in single) the rounding recovers it exactly and C is exact.  A
+//      lag whose g/N lies more than 1/4 from an integer is counted as inexact.
 //   6. k_radial_finish: bin means, C(b) = sum_G / (N n_b), S(b) = sum_P / (N n_b), and the
 //      length l at which C first crosses c for r <= L/2.
+//
+// Binning: the lanes of a warp take consecutive elements of a row, whose bins form runs; a
+// segmented warp scan sums each run and its last lane adds the sum to the CTA's bins in
+// shared memory with one atomic, and the CTA's bins go to the global sums at the end.  The
+// number of vectors per bin does not depend on the state and is counted once per context.
+// The transform buffer and cuFFT's work area stay allocated in the context between calls.
 //
 // Bins: components as minimal images, squared length D, bin round(sqrt(D)) computed exactly
 // as (isqrt(4D) + 1) / 2.
@@ -53,6 +59,17 @@ struct Cx<double> {
     using type = cufftDoubleComplex;
 };
 
+template <typename T>
+struct Pair;
+template <>
+struct Pair<float> {
+    using type = float2;
+};
+template <>
+struct Pair<double> {
+    using type = double2;
+};
+
 constexpr int RAD_THREADS = 256;
 
 }  // namespace
@@ -60,7 +77,7 @@ constexpr int RAD_THREADS = 256;
 int64_t radial_nbins(int L) { return (int64_t)((isqrt_exact(3 * L * L) + 1) >> 1) + 1; }
 
 // Loops below run over rows (y, z) in a grid-stride loop and over the row's elements with
-// the CTA's threads, so no 64-bit division is needed per element.
+// the CTA's warps, lane = consecutive element, so no 64-bit division is needed per element.
 
 // 1. A thread takes a pair of sites (x = 2k, 2k+1) of a row: both share compressed index k,
 // one on each sublattice.
@@ -77,97 +94,148 @@ __global__ void k_unpack_real(const uint32_t *lat_r, T *buf, Geom g, int64_t P)
         for (int k = threadIdx.x; k < H; k += blockDim.x) {
             const int bit = k & 31;
             const uint32_t w0 = __ldg(r0 + (k >> 5)), w1 = __ldg(r1 + (k >> 5));
-            dst[2 * k] = ((w0 >> bit) & 1u) ? T(1) : T(-1);
-            dst[2 * k + 1] = ((w1 >> bit) & 1u) ? T(1) : T(-1);
+            typename Pair<T>::type v;  // one aligned store of the two sites (rows of even length)
+            v.x = ((w0 >> bit) & 1u) ? T(1) : T(-1);
+            v.y = ((w1 >> bit) & 1u) ? T(1) : T(-1);
+            *reinterpret_cast<typename Pair<T>::type *>(dst + 2 * k) = v;
         }
     }
 }
 
-// Per-CTA bins in shared memory, flushed to the global sums at the end.
+// The 32 lanes hold (bin b, value v) of consecutive elements (b < 0: no element).  Runs of
+// equal b are summed by a segmented inclusive scan in type V; each run's last lane adds its
+// sum to hist[b] (type H).
+template <typename V, typename H>
+__device__ __forceinline__ void run_add(int b, V v, H *hist)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int bp = __shfl_up_sync(FULL, b, 1);
+    const unsigned heads = __ballot_sync(FULL, lane == 0 || bp != b);
+    const int seg = __popc(heads & (FULL >> (31 - lane)));  // run number of this lane
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const V vo = __shfl_up_sync(FULL, v, d);
+        const int so = __shfl_up_sync(FULL, seg, d);
+        if (lane >= d && so == seg) v += vo;
+    }
+    const int bn = __shfl_down_sync(FULL, b, 1);
+    if ((lane == 31 || bn != b) && b >= 0) atomicAdd(&hist[b], (H)v);
+}
+
+template <typename V>
+__device__ __forceinline__ void zero_bins(V *h, int nb)
+{
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) h[i] = V(0);
+    __syncthreads();
+}
+
+template <typename V>
+__device__ __forceinline__ void flush_bins(const V *h, V *global, int nb)
+{
+    __syncthreads();
+    for (int i = threadIdx.x; i < nb; i += blockDim.x)
+        if (h[i] != V(0)) atomicAdd(&global[i], h[i]);
+}
+
+// 3. |F|^2 per mode of the half spectrum; S sums per bin; (P, 0) written back.
 template <typename T>
 __global__ void __launch_bounds__(RAD_THREADS) k_power(typename Cx<T>::type *F, int L, int nb, double *sumS)
 {
     extern __shared__ double hs[];
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) hs[i] = 0.0;
-    __syncthreads();
+    zero_bins(hs, nb);
     const int H1 = L / 2 + 1;
+    const int lane = threadIdx.x & 31;
     for (int row = blockIdx.x; row < L * L; row += gridDim.x) {
         const int ny = min_image(row % L, L), nz = min_image(row / L, L);
         const int dyz = ny * ny + nz * nz;
         typename Cx<T>::type *Fr = F + (int64_t)row * H1;
-        for (int nx = threadIdx.x; nx < H1; nx += blockDim.x) {
-            const typename Cx<T>::type f = Fr[nx];
-            const double p = (double)f.x * (double)f.x + (double)f.y * (double)f.y;
-            const double w = (nx == 0 || nx == L / 2) ? 1.0 : 2.0;
-            atomicAdd(&hs[bin_of(nx * nx + dyz)], w * p);
-            typename Cx<T>::type o;
-            o.x = (T)p;
-            o.y = T(0);
-            Fr[nx] = o;
+        for (int x0 = threadIdx.x & ~31; x0 < H1; x0 += blockDim.x) {
+            const int nx = x0 + lane;
+            int b = -1;
+            T wp = T(0);  // single precision stays in fp32 up to the per-run double add
+            if (nx < H1) {
+                const typename Cx<T>::type f = Fr[nx];
+                const T p = f.x * f.x + f.y * f.y;
+                wp = (nx == 0 || nx == L / 2) ? p : T(2) * p;  // 0 < nx < L/2: also the partner -q
+                b = bin_of(nx * nx + dyz);
+                typename Cx<T>::type o;
+                o.x = p;
+                o.y = T(0);
+                Fr[nx] = o;
+            }
+            run_add<T, double>(b, wp, hs);
         }
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < nb; i += blockDim.x)
-        if (hs[i] != 0.0) atomicAdd(&sumS[i], hs[i]);
+    flush_bins(hs, sumS, nb);
 }
 
-// EXACT: round g/N to the integer G(k) and sum integers (double precision transforms).
-template <typename T, bool EXACT>
+// 5. G(k) = rint(g/N) per lag, summed per bin in int64.
+template <typename T>
 __global__ void __launch_bounds__(RAD_THREADS) k_radial_corr(const T *g, int L, int64_t P, int nb, double invN,
-                                                             long long *sumG, double *sumC,
-                                                             unsigned long long *count, unsigned long long *inexact)
+                                                             unsigned long long *sumG, unsigned long long *inexact)
 {
-    extern __shared__ long long hsm[];
-    long long *hG = hsm;                                              // EXACT: integer sums
-    double *hC = reinterpret_cast<double *>(hsm);                     // otherwise: real sums
-    unsigned long long *hn = reinterpret_cast<unsigned long long *>(hsm + nb);
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
-        hG[i] = 0;
-        hn[i] = 0ull;
-    }
-    __syncthreads();
+    extern __shared__ unsigned long long hg[];
+    zero_bins(hg, nb);
+    const int lane = threadIdx.x & 31;
     unsigned long long bad = 0ull;
     for (int row = blockIdx.x; row < L * L; row += gridDim.x) {
         const int dy = min_image(row % L, L), dz = min_image(row / L, L);
         const int dyz = dy * dy + dz * dz;
         const T *gr = g + (int64_t)row * P;
-        for (int x = threadIdx.x; x < L; x += blockDim.x) {
-            const int dx = min_image(x, L);
-            const int b = bin_of(dx * dx + dyz);
-            const double v = (double)gr[x] * invN;
-            if (EXACT) {
-                const double r = rint(v);
-                if (fabs(v - r) > 0.25) ++bad;
-                atomicAdd(reinterpret_cast<unsigned long long *>(&hG[b]), (unsigned long long)(long long)r);
-            } else {
-                atomicAdd(&hC[b], v);
+        for (int x0 = threadIdx.x & ~31; x0 < L; x0 += blockDim.x) {
+            const int x = x0 + lane;
+            int b = -1;
+            unsigned long long G = 0ull;
+            if (x < L) {
+                const int dx = min_image(x, L);
+                b = bin_of(dx * dx + dyz);
+                // invN is a power of two, so the scaling is exact in either precision
+                const T v = gr[x] * (T)invN;
+                const T r = rint(v);
+                if (fabs(v - r) > T(0.25)) ++bad;
+                // two's complement: the unsigned sums wrap to the signed result
+                G = (fabs(r) < T(2147483520)) ? (unsigned long long)(long long)(int)r
+                                               : (unsigned long long)(long long)r;
             }
-            atomicAdd(&hn[b], 1ull);
+            run_add<unsigned long long, unsigned long long>(b, G, hg);
         }
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
-        if (hn[i] == 0ull) continue;
-        if (EXACT)
-            atomicAdd(reinterpret_cast<unsigned long long *>(&sumG[i]), (unsigned long long)hG[i]);
-        else
-            atomicAdd(&sumC[i], hC[i]);
-        atomicAdd(&count[i], hn[i]);
-    }
-    if (EXACT && bad) atomicAdd(inexact, bad);
+    flush_bins(hg, sumG, nb);
+    if (bad) atomicAdd(inexact, bad);
 }
 
-// out = [C(0..nb-1), S(0..nb-1), l]; cnt = [n_b (nb), inexact lags].
-__global__ void k_radial_finish(int L, int nb, int exact, double c, const long long *sumG, const double *sumC,
-                                const double *sumS, const unsigned long long *count,
-                                const unsigned long long *inexact, double *out, int64_t *cnt)
+// Vectors per bin (independent of the state; once per context).
+__global__ void __launch_bounds__(RAD_THREADS) k_radial_count(int L, int nb, unsigned long long *count)
+{
+    extern __shared__ unsigned long long hc[];
+    zero_bins(hc, nb);
+    const int lane = threadIdx.x & 31;
+    for (int row = blockIdx.x; row < L * L; row += gridDim.x) {
+        const int dy = min_image(row % L, L), dz = min_image(row / L, L);
+        const int dyz = dy * dy + dz * dz;
+        for (int x0 = threadIdx.x & ~31; x0 < L; x0 += blockDim.x) {
+            const int x = x0 + lane;
+            int b = -1;
+            if (x < L) {
+                const int dx = min_image(x, L);
+                b = bin_of(dx * dx + dyz);
+            }
+            run_add<unsigned long long, unsigned long long>(b, b >= 0 ? 1ull : 0ull, hc);
+        }
+    }
+    flush_bins(hc, count, nb);
+}
+
+// 6. out = [C(0..nb-1), S(0..nb-1), l]; cnt = [n_b (nb), inexact lags].
+__global__ void k_radial_finish(int L, int nb, double c, const unsigned long long *sumG, const double *sumS,
+                                const unsigned long long *count, const unsigned long long *inexact, double *out,
+                                int64_t *cnt)
 {
     const double N = (double)L * (double)L * (double)L;
     for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-        const double n = (double)count[b];
-        const double denom = __dmul_rn(N, n);
-        const double num = exact ? (double)sumG[b] : sumC[b];  // the bin's sum of G(k)
-        out[b] = count[b] ? __ddiv_rn(num, denom) : 0.0;
+        const double denom = __dmul_rn(N, (double)count[b]);
+        out[b] = count[b] ? __ddiv_rn((double)(long long)sumG[b], denom) : 0.0;
         out[nb + b] = count[b] ? __ddiv_rn(sumS[b], denom) : 0.0;
         cnt[b] = (int64_t)count[b];
     }
@@ -182,7 +250,7 @@ __global__ void k_radial_finish(int L, int nb, int exact, double c, const long l
             }
         }
         out[2 * nb] = ell;
-        cnt[nb] = exact ? (int64_t)*inexact : -1;
+        cnt[nb] = (int64_t)*inexact;
     }
 }
 
@@ -192,13 +260,31 @@ struct RadialPlans {
     bool made[2] = {false, false};
     cufftHandle fwd[2] = {0, 0}, inv[2] = {0, 0};
     size_t work[2] = {0, 0};
+    char *buf = nullptr;  // transform buffer (grown to the largest precision used)
+    size_t buf_bytes = 0;
+    char *wk = nullptr;   // cuFFT work area
+    size_t wk_bytes = 0;
+    unsigned long long *count = nullptr;  // vectors per bin (counted at the first call)
+    char *acc = nullptr;                  // per-call sums: sumG, sumS, inexact
 };
 
 RadialPlans *radial_plans_create() { return new (std::nothrow) RadialPlans(); }
 
-void radial_plans_destroy(RadialPlans *p)
+void radial_release(RadialPlans *p, cudaStream_t s)
 {
     if (!p) return;
+    if (p->buf) cudaFreeAsync(p->buf, s);
+    if (p->wk) cudaFreeAsync(p->wk, s);
+    p->buf = p->wk = nullptr;
+    p->buf_bytes = p->wk_bytes = 0;
+}
+
+void radial_plans_destroy(RadialPlans *p, cudaStream_t s)
+{
+    if (!p) return;
+    radial_release(p, s);
+    if (p->count) cudaFreeAsync(p->count, s);
+    if (p->acc) cudaFreeAsync(p->acc, s);
     for (int i = 0; i < 2; ++i)
         if (p->made[i]) {
             cufftDestroy(p->fwd[i]);
@@ -241,6 +327,23 @@ size_t radial_scratch_bytes(int L, int prec)
     return (size_t)L * (size_t)L * (size_t)(L / 2 + 1) * 2 * elem;
 }
 
+// Grow a cached device allocation to at least `bytes` (stream-ordered).
+static cudaError_t ensure(char **ptr, size_t *have, size_t bytes, cudaStream_t s)
+{
+    if (*have >= bytes && (*ptr || bytes == 0)) return cudaSuccess;
+    if (*ptr) cudaFreeAsync(*ptr, s);
+    *ptr = nullptr;
+    *have = 0;
+    if (bytes == 0) return cudaSuccess;
+    cudaError_t e = cudaMallocAsync((void **)ptr, bytes, s);
+    if (e != cudaSuccess) {
+        *ptr = nullptr;
+        return e;
+    }
+    *have = bytes;
+    return cudaSuccess;
+}
+
 template <typename T>
 static cudaError_t run_radial(RadialPlans *p, const uint32_t *lat_r, int L, double c, double *out, int64_t *cnt,
                               cudaStream_t s, int64_t *launches, int *cufft_status)
@@ -254,83 +357,72 @@ static cudaError_t run_radial(RadialPlans *p, const uint32_t *lat_r, int L, doub
         *cufft_status = cs;
         return cudaErrorUnknown;
     }
-    const size_t data_bytes = radial_scratch_bytes(L, prec);
-    const size_t acc_bytes = (size_t)nb * (3 * sizeof(double) + sizeof(unsigned long long)) + 64;
-    char *buf = nullptr, *work = nullptr, *acc = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&buf, data_bytes, s);
-    if (e != cudaSuccess) return e;
-    if (p->work[prec] && (e = cudaMallocAsync((void **)&work, p->work[prec], s)) != cudaSuccess) {
-        cudaFreeAsync(buf, s);
+    cudaError_t e;
+    if ((e = ensure(&p->buf, &p->buf_bytes, radial_scratch_bytes(L, prec), s)) != cudaSuccess) return e;
+    if ((e = ensure(&p->wk, &p->wk_bytes, p->work[prec], s)) != cudaSuccess) return e;
+    const size_t acc_bytes = (size_t)nb * 2 * sizeof(double) + 64;
+    if (!p->acc && (e = cudaMallocAsync((void **)&p->acc, acc_bytes, s)) != cudaSuccess) {
+        p->acc = nullptr;
         return e;
     }
-    if ((e = cudaMallocAsync((void **)&acc, acc_bytes, s)) != cudaSuccess) {
-        cudaFreeAsync(buf, s);
-        if (work) cudaFreeAsync(work, s);
-        return e;
-    }
-    auto cleanup = [&](cudaError_t err) {
-        cudaFreeAsync(acc, s);
-        if (work) cudaFreeAsync(work, s);
-        cudaFreeAsync(buf, s);
-        return err;
-    };
-    long long *sumG = reinterpret_cast<long long *>(acc);
-    double *sumC = reinterpret_cast<double *>(acc);  // same storage: one of the two is used
-    double *sumS = reinterpret_cast<double *>(acc) + nb;
-    unsigned long long *count = reinterpret_cast<unsigned long long *>(acc) + 2 * nb;
-    unsigned long long *inexact = count + nb;
-    if ((e = cudaMemsetAsync(acc, 0, acc_bytes, s)) != cudaSuccess) return cleanup(e);
+    unsigned long long *sumG = reinterpret_cast<unsigned long long *>(p->acc);
+    double *sumS = reinterpret_cast<double *>(p->acc) + nb;
+    unsigned long long *inexact = reinterpret_cast<unsigned long long *>(p->acc) + 2 * nb;
+    if ((e = cudaMemsetAsync(p->acc, 0, acc_bytes, s)) != cudaSuccess) return e;
     int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     const unsigned grid = (unsigned)(sms * 4);
+    const size_t smem = (size_t)nb * sizeof(double);
+    if (!p->count) {
+        if ((e = cudaMallocAsync((void **)&p->count, sizeof(unsigned long long) * nb, s)) != cudaSuccess) {
+            p->count = nullptr;
+            return e;
+        }
+        if ((e = cudaMemsetAsync(p->count, 0, sizeof(unsigned long long) * nb, s)) != cudaSuccess) return e;
+        if ((e = cudaFuncSetAttribute(k_radial_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+            cudaSuccess)
+            return e;
+        k_radial_count<<<grid, RAD_THREADS, smem, s>>>(L, nb, p->count);
+        if (launches) *launches += 1;
+    }
 
-    k_unpack_real<T><<<grid, RAD_THREADS, 0, s>>>(lat_r, reinterpret_cast<T *>(buf), g, P);
+    k_unpack_real<T><<<grid, RAD_THREADS, 0, s>>>(lat_r, reinterpret_cast<T *>(p->buf), g, P);
     cufftHandle f = p->fwd[prec], iv = p->inv[prec];
     if ((cs = cufftSetStream(f, s)) != CUFFT_SUCCESS || (cs = cufftSetStream(iv, s)) != CUFFT_SUCCESS ||
-        (cs = cufftSetWorkArea(f, work)) != CUFFT_SUCCESS || (cs = cufftSetWorkArea(iv, work)) != CUFFT_SUCCESS) {
+        (cs = cufftSetWorkArea(f, p->wk)) != CUFFT_SUCCESS || (cs = cufftSetWorkArea(iv, p->wk)) != CUFFT_SUCCESS) {
         *cufft_status = cs;
-        return cleanup(cudaErrorUnknown);
+        return cudaErrorUnknown;
     }
     using C = typename Cx<T>::type;
     if (prec)
-        cs = cufftExecD2Z(f, reinterpret_cast<cufftDoubleReal *>(buf), reinterpret_cast<cufftDoubleComplex *>(buf));
+        cs = cufftExecD2Z(f, reinterpret_cast<cufftDoubleReal *>(p->buf), reinterpret_cast<cufftDoubleComplex *>(p->buf));
     else
-        cs = cufftExecR2C(f, reinterpret_cast<cufftReal *>(buf), reinterpret_cast<cufftComplex *>(buf));
+        cs = cufftExecR2C(f, reinterpret_cast<cufftReal *>(p->buf), reinterpret_cast<cufftComplex *>(p->buf));
     if (cs != CUFFT_SUCCESS) {
         *cufft_status = cs;
-        return cleanup(cudaErrorUnknown);
+        return cudaErrorUnknown;
     }
-    const size_t smem_p = (size_t)nb * sizeof(double);
-    if ((e = cudaFuncSetAttribute(k_power<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_p)) != cudaSuccess)
-        return cleanup(e);
-    k_power<T><<<grid, RAD_THREADS, smem_p, s>>>(reinterpret_cast<C *>(buf), L, nb, sumS);
+    if ((e = cudaFuncSetAttribute(k_power<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+        return e;
+    k_power<T><<<grid, RAD_THREADS, smem, s>>>(reinterpret_cast<C *>(p->buf), L, nb, sumS);
     if (prec)
-        cs = cufftExecZ2D(iv, reinterpret_cast<cufftDoubleComplex *>(buf), reinterpret_cast<cufftDoubleReal *>(buf));
+        cs = cufftExecZ2D(iv, reinterpret_cast<cufftDoubleComplex *>(p->buf), reinterpret_cast<cufftDoubleReal *>(p->buf));
     else
-        cs = cufftExecC2R(iv, reinterpret_cast<cufftComplex *>(buf), reinterpret_cast<cufftReal *>(buf));
+        cs = cufftExecC2R(iv, reinterpret_cast<cufftComplex *>(p->buf), reinterpret_cast<cufftReal *>(p->buf));
     if (cs != CUFFT_SUCCESS) {
         *cufft_status = cs;
-        return cleanup(cudaErrorUnknown);
+        return cudaErrorUnknown;
     }
-    const size_t smem_c = (size_t)nb * 2 * sizeof(long long);
     const double invN = 1.0 / ((double)L * (double)L * (double)L);  // exact: N is a power of two
-    if (prec) {
-        if ((e = cudaFuncSetAttribute(k_radial_corr<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem_c)) != cudaSuccess)
-            return cleanup(e);
-        k_radial_corr<T, true><<<grid, RAD_THREADS, smem_c, s>>>(reinterpret_cast<const T *>(buf), L, P, nb, invN,
-                                                                  sumG, sumC, count, inexact);
-    } else {
-        if ((e = cudaFuncSetAttribute(k_radial_corr<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem_c)) != cudaSuccess)
-            return cleanup(e);
-        k_radial_corr<T, false><<<grid, RAD_THREADS, smem_c, s>>>(reinterpret_cast<const T *>(buf), L, P, nb, invN,
-                                                                   sumG, sumC, count, inexact);
-    }
-    k_radial_finish<<<1, 256, 0, s>>>(L, nb, prec, c, sumG, sumC, sumS, count, inexact, out, cnt);
+    if ((e = cudaFuncSetAttribute(k_radial_corr<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+        cudaSuccess)
+        return e;
+    k_radial_corr<T><<<grid, RAD_THREADS, smem, s>>>(reinterpret_cast<const T *>(p->buf), L, P, nb, invN, sumG,
+                                                       inexact);
+    k_radial_finish<<<1, 256, 0, s>>>(L, nb, c, sumG, sumS, p->count, inexact, out, cnt);
     if (launches) *launches += 4;  // own kernels; the two cuFFT executions are library launches
-    return cleanup(cudaGetLastError());
+    return cudaGetLastError();
 }
 
 cudaError_t launch_radial(RadialPlans *p, const uint32_t *lat_r, int L, int precision, double c, double *out,

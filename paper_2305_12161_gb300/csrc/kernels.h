@@ -67,14 +67,15 @@ cudaError_t launch_sweeps_dcb(uint32_t *lat, int L, int R, uint64_t seed, int ru
                               int cycle, const DcbGeom &d, cudaStream_t s, int64_t *launches);
 
 // Radially averaged 3-d correlation and structure factor of one lattice (lat_r: replica's
-// packed store) through cuFFT; precision 0: single, 1: double (exact integer G(k)).
+// packed store) through cuFFT; precision 0: single, 1: double.
 // out (device): [C(0..nb-1), S(0..nb-1), l]; cnt (device): [n_b (nb), inexact lags].
-// Allocates, stream-ordered, radial_scratch_bytes(L, precision) plus cuFFT's work area and
-// frees them before returning.  On a cuFFT failure returns cudaErrorUnknown with the cuFFT
-// status in *cufft_status.
+// Allocates, stream-ordered, radial_scratch_bytes(L, precision) plus cuFFT's work area at the
+// first call and keeps them in *p (radial_release frees them).  On a cuFFT failure returns
+// cudaErrorUnknown with the cuFFT status in *cufft_status.
 struct RadialPlans;
 RadialPlans *radial_plans_create();
-void radial_plans_destroy(RadialPlans *p);
+void radial_release(RadialPlans *p, cudaStream_t s);
+void radial_plans_destroy(RadialPlans *p, cudaStream_t s);
 int64_t radial_nbins(int L);
 size_t radial_scratch_bytes(int L, int precision);
 cudaError_t launch_radial(RadialPlans *p, const uint32_t *lat_r, int L, int precision, double c, double *out,

@@ -75,6 +75,7 @@ def lib() -> ctypes.CDLL:
                 "ising_measure": (ctypes.c_int, [vp, vp]),
                 "ising_measure_ex": (ctypes.c_int, [vp, vp, vp, ctypes.c_double, ctypes.c_uint]),
                 "ising_radial_bins": (ctypes.c_int64, [ctypes.c_int]),
+                "ising_release_scratch": (ctypes.c_int, [vp]),
                 "ising_measure_radial": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, vp, vp,
                                                         vp, vp, vp]),
                 "ising_get_spins": (ctypes.c_int, [vp, ctypes.c_int, vp]),
@@ -236,7 +237,7 @@ class Ising:
 
     def measure_radial(self, replica: int = 0, precision: int = FFT_SINGLE, c: float = 0.5) -> dict:
         """Radially averaged 3-d correlation C(b), structure factor S(b), vectors per bin,
-        the length at which C crosses c, and (double precision) the number of inexact lags."""
+        the length at which C crosses c, and the number of inexact lags (0: C is exact)."""
         nb = ising_radial_bins(self.L)
         C = np.empty(nb, dtype=np.float64)
         S = np.empty(nb, dtype=np.float64)
@@ -247,6 +248,10 @@ class Ising:
                                                n.ctypes.data, ctypes.addressof(ell), ctypes.addressof(bad)),
                     "ising_measure_radial")
         return {"C": C, "S": S, "count": n, "ell": ell.value, "inexact": bad.value}
+
+    def release_scratch(self) -> None:
+        """Free the measurement scratch kept in the context (radial FFT buffer, etc.)."""
+        self._check(lib().ising_release_scratch(self._h), "ising_release_scratch")
 
     def measure_device(self, rec, derived=None, c: float = 0.5, connected: bool = False, corr: bool = True) -> None:
         """Enqueue a measurement into device buffers (no synchronisation)."""
