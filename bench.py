@@ -335,6 +335,41 @@ def run_radial_case(args):
     print(json.dumps(out))
 
 
+def run_hist_case(args):
+    """Statistical cross-check against the paper's domain-size histogram (Supplementary
+    Discussion II): --runs independent L=256 lattices (seeds 1..runs) quenched with the 01-cycle
+    checkerboard to rescaled time 4000 MCS (2286 checkerboard MCS at the factor 1.75), then
+    l from the radially averaged C (fp32 FFTs) and from the axis C of every lattice."""
+    import torch
+
+    import __graft_entry__
+    from paper_2305_12161_gb300 import ising
+    __graft_entry__.build()
+    L, runs = 256, args.runs
+    mcs = round(4000 / 1.75)
+    stream = torch.cuda.Stream()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    with ising.Ising(L, replicas=runs, seed=1, stream=stream) as q:
+        a.record(stream)
+        q.sweep(mcs)
+        b.record(stream)
+        _, der = q.measure_ex(c=0.5)
+        ms_sweep = a.elapsed_time(b)
+        t0 = time.perf_counter()
+        ell_rad = [q.measure_radial(replica=r, precision=ising.FFT_SINGLE)["ell"] for r in range(runs)]
+        s_rad = time.perf_counter() - t0
+    import numpy as np
+    er, ea = np.array(ell_rad), der[:, 3]
+    print(json.dumps({
+        "case": "hist", "metric": "mean domain size l at rescaled t=4000 MCS, L=256 (paper: 19.9 checkerboard)",
+        "runs": runs, "mcs": mcs, "mean_ell_radial": float(er.mean()), "std_ell_radial": float(er.std(ddof=1)),
+        "sem_ell_radial": float(er.std(ddof=1) / np.sqrt(runs)), "mean_ell_axis": float(ea.mean()),
+        "sem_ell_axis": float(ea.std(ddof=1) / np.sqrt(runs)),
+        "quantiles_radial": [float(v) for v in np.quantile(er, [0.05, 0.25, 0.5, 0.75, 0.95])],
+        "sweep_updates_per_ns": runs * L**3 * mcs / (ms_sweep * 1e-3) / 1e9, "radial_s_total": s_rad}))
+
+
 def run_serve_case(args):
     """Continuous-batching serving on a finite seeded trace: Poisson arrivals at 20/s,
     L log-uniform on {64..1024}, t_max = 10^U[3,5] MCS, 1-16 replicas, 12 log-spaced
@@ -380,7 +415,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--block-y", type=int, default=16, help="dcb case: block rows along y")
     ap.add_argument("--block-z", type=int, default=8, help="dcb case: block planes along z")
-    ap.add_argument("--case", default="bench", choices=["bench", "quench", "serve", "batch", "dcb", "radial"],
+    ap.add_argument("--runs", type=int, default=1000, help="hist case: independent L=256 runs")
+    ap.add_argument("--case", default="bench", choices=["bench", "quench", "serve", "batch", "dcb", "radial", "hist"],
                     help="quench: init + --mcs sweeps + one measurement, untimed (for profilers); "
                          "serve: the serving loop on the first --requests arrivals of the seeded trace")
     ap.add_argument("--requests", type=int, default=24)
@@ -402,6 +438,9 @@ def main():
         return
     if args.case == "radial":
         run_radial_case(args)
+        return
+    if args.case == "hist":
+        run_hist_case(args)
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
