@@ -416,6 +416,8 @@ def main():
     ap.add_argument("--block-y", type=int, default=16, help="dcb case: block rows along y")
     ap.add_argument("--block-z", type=int, default=8, help="dcb case: block planes along z")
     ap.add_argument("--runs", type=int, default=1000, help="hist case: independent L=256 runs")
+    ap.add_argument("--sweep-config", default="", help="variant,tile_y,tile_z,depth instead of the autotuner "
+                                                        "(for launch lists: no tuning launches)")
     ap.add_argument("--case", default="bench", choices=["bench", "quench", "serve", "batch", "dcb", "radial", "hist"],
                     help="quench: init + --mcs sweeps + one measurement, untimed (for profilers); "
                          "serve: the serving loop on the first --requests arrivals of the seeded trace")
@@ -471,7 +473,11 @@ def main():
     N = L**3
     seed = 1 + 1000 * rank
     stream = torch.cuda.Stream()
-    tuned = ising.ising_tune_sweep(L, 1, probe_mcs=8)  # the project's autotuner picks the kernel
+    if args.sweep_config:  # fixed kernel configuration (variant,tile_y,tile_z,depth), no tuning launches
+        v, ty, tz, dp = (int(x) for x in args.sweep_config.split(","))
+        tuned = {"variant": v, "tile_y": ty, "tile_z": tz, "depth": dp, "ms_per_mcs": None}
+    else:
+        tuned = ising.ising_tune_sweep(L, 1, probe_mcs=8)  # the project's autotuner picks the kernel
     q = ising.Ising(L, replicas=1, seed=seed, stream=stream, variant=tuned["variant"], tile_y=tuned["tile_y"],
                     tile_z=tuned["tile_z"], depth=tuned["depth"])
     RL = q.record_len
