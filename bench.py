@@ -581,11 +581,12 @@ def main():
     n_meas = len(meas_events)
     meas_avg_s = meas_ms * 1e-3 / n_meas
     # Bound of the correlation kernel, which sums XOR words on two pipes at once.  Counted from
-    # the source: a POPC-path word is 1 bit count (16 lanes per SM per clock) + 2 logic/add
-    # ops (64 lanes per SM per clock); a carry-save word is 1/8 bit count + 23/8 logic/add ops
-    # (8 XORs, 7 adders of two 3-input ops each, 1 add per 8 words).  The best split f of
-    # words on the POPC path balances both pipes; it gives 26.7 words per SM per clock.
-    p_pop, a_pop, p_csa, a_csa = 1.0, 2.0, 1.0 / 8, 23.0 / 8
+    # the source: a POPC-path word is 1 bit count (16 lanes per SM per clock) + 1 XOR on the
+    # integer ALU (64 lanes per SM per clock), its add issuing as a multiply-add on the
+    # otherwise idle FMA pipe; a carry-save word is 1/8 bit count + 22/8 ALU ops (8 XORs and
+    # 7 adders of two 3-input ops per 8 words).  The best split f of words on the POPC path
+    # balances the two pipes: f = 0.43, 32 words per SM per clock.
+    p_pop, a_pop, p_csa, a_csa = 1.0, 1.0, 1.0 / 8, 22.0 / 8
     f_pop = (a_csa / 64 - p_csa / 16) / ((p_pop - p_csa) / 16 + (a_csa - a_pop) / 64)
     words_per_clk = 16 / (f_pop * p_pop + (1 - f_pop) * p_csa)
     popc_peak = 152 * words_per_clk * pk["sm_max_mhz"] * 1e6 / 1e12  # T word pairs/s

@@ -147,8 +147,18 @@ __device__ __forceinline__ void load_panel_yz(const uint32_t *S0, const uint32_t
 
 // Three CTAs per SM (80 registers): with that bound the compiler keeps the carry-save
 // registers without spilling; two CTAs with more registers measured 3% slower.
+// t + p * one with `one` = 1 passed at run time: the compiler cannot fold the product, so the
+// sum issues as an integer multiply-add on the FMA pipe, which this kernel otherwise leaves
+// idle, instead of an add on the integer ALU pipe that the XORs and adders saturate.
+__device__ __forceinline__ uint32_t mad_u32(uint32_t p, uint32_t one, uint32_t t)
+{
+    uint32_t r;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(p), "r"(one), "r"(t));
+    return r;
+}
+
 template <int NT, int RT>
-__global__ void __launch_bounds__(NT, 3) k_corr(const uint32_t *lat, Geom g, int64_t *rec)
+__global__ void __launch_bounds__(NT, 3) k_corr(const uint32_t *lat, Geom g, int64_t *rec, uint32_t one)
 {
     extern __shared__ uint32_t csm[];
     const int axis = blockIdx.z;
@@ -213,6 +223,11 @@ __global__ void __launch_bounds__(NT, 3) k_corr(const uint32_t *lat, Geom g, int
             // pipes work at once; the choice is per warp, so no warp diverges.  (Measured at
             // L=2048: 4 of 8 on carry-save 148 ms, 3 of 8 166 ms, none 178 ms, per-item
             // alternation 7% slower than 3 of 8.)
+            // Lags start at r0 = 1 + 8i, so the window's next word r0 + 7 + j + u sits at the
+            // padded index 9(i + 1 + j/8) + u and the column word j + u at 9(j/8) + u: one
+            // base pointer per 8-word step, the eight loads at immediate offsets.
+            const uint32_t *wp = col + corr_pad(r0 + RT - 1);
+            const uint32_t *ap = col;
             if (RT == 8 && (wid & 7) >= 4) {
                 // Harley-Seal carry-save accumulation per lag: eight XOR words pass through
                 // seven carry-save adders into (ones, twos, fours) and one "eights" word,
@@ -220,12 +235,11 @@ __global__ void __launch_bounds__(NT, 3) k_corr(const uint32_t *lat, Geom g, int
                 uint32_t ones[RT], twos[RT], fours[RT], v[RT], twosA[RT], foursA[RT];
 #pragma unroll
                 for (int k = 0; k < RT; ++k) ones[k] = twos[k] = fours[k] = total[k] = 0u;
-                for (int j = 0; j < L; j += RT) {
+                for (int j = 0; j < L; j += RT, wp += 9, ap += 9) {
 #pragma unroll
                     for (int u = 0; u < RT; ++u) {
-                        const int jj = j + u;
-                        if (u != 0 || j != 0) win[(u + RT - 1) % RT] = col[corr_pad(r0 + jj + RT - 1)];
-                        const uint32_t a = col[corr_pad(jj)];
+                        if (u != 0 || j != 0) win[(u + RT - 1) % RT] = wp[u];
+                        const uint32_t a = ap[u];
 #pragma unroll
                         for (int k = 0; k < RT; ++k) {
                             const uint32_t x = a ^ win[(u + k) % RT];
@@ -245,7 +259,7 @@ __global__ void __launch_bounds__(NT, 3) k_corr(const uint32_t *lat, Geom g, int
                                     } else {
                                         const uint32_t t8 = (fours[k] & foursA[k]) | (t4 & (fours[k] ^ foursA[k]));
                                         fours[k] = fours[k] ^ foursA[k] ^ t4;
-                                        total[k] += __popc(t8);
+                                        total[k] = mad_u32(__popc(t8), one, total[k]);
                                     }
                                 }
                             }
@@ -258,14 +272,26 @@ __global__ void __launch_bounds__(NT, 3) k_corr(const uint32_t *lat, Geom g, int
             } else {
 #pragma unroll
                 for (int k = 0; k < RT; ++k) total[k] = 0u;
-                for (int j = 0; j < L; j += RT) {
+                if (RT == 8) {
+                    for (int j = 0; j < L; j += RT, wp += 9, ap += 9) {
 #pragma unroll
-                    for (int u = 0; u < RT; ++u) {
-                        const int jj = j + u;
-                        if (u != 0 || j != 0) win[(u + RT - 1) % RT] = col[corr_pad(r0 + jj + RT - 1)];
-                        const uint32_t a = col[corr_pad(jj)];
+                        for (int u = 0; u < RT; ++u) {
+                            if (u != 0 || j != 0) win[(u + RT - 1) % RT] = wp[u];
+                            const uint32_t a = ap[u];
 #pragma unroll
-                        for (int k = 0; k < RT; ++k) total[k] += __popc(a ^ win[(u + k) % RT]);
+                            for (int k = 0; k < RT; ++k) total[k] = mad_u32(__popc(a ^ win[(u + k) % RT]), one, total[k]);
+                        }
+                    }
+                } else {
+                    for (int j = 0; j < L; j += RT) {
+#pragma unroll
+                        for (int u = 0; u < RT; ++u) {
+                            const int jj = j + u;
+                            if (u != 0 || j != 0) win[(u + RT - 1) % RT] = col[corr_pad(r0 + jj + RT - 1)];
+                            const uint32_t a = col[corr_pad(jj)];
+#pragma unroll
+                            for (int k = 0; k < RT; ++k) total[k] += __popc(a ^ win[(u + k) % RT]);
+                        }
                     }
                 }
             }
@@ -307,7 +333,7 @@ static cudaError_t launch_corr(const uint32_t *lat, const Geom &g, int R, int64_
     int64_t want = ((int64_t)occ * sms) / ((int64_t)3 * R);
     if (want < 1) want = 1;
     if (panels > want) panels = want;
-    k_corr<256, RT><<<dim3((unsigned)panels, (unsigned)R, 3), 256, smem, s>>>(lat, g, rec);
+    k_corr<256, RT><<<dim3((unsigned)panels, (unsigned)R, 3), 256, smem, s>>>(lat, g, rec, 1u);
     return cudaGetLastError();
 }
 
