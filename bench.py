@@ -144,7 +144,11 @@ def run_quench_case(args):
     import __graft_entry__
     from paper_2305_12161_gb300 import ising
     __graft_entry__.build()
-    with ising.Ising(args.L, replicas=1, seed=1, corr=args.corr) as q:
+    kw = {}
+    if args.sweep_config:
+        v, ty, tz, dp = (int(x) for x in args.sweep_config.split(","))
+        kw = dict(variant=v, tile_y=ty, tile_z=tz, depth=dp)
+    with ising.Ising(args.L, replicas=1, seed=1, corr=args.corr, **kw) as q:
         q.sweep(args.mcs)
         rec, der = q.measure_ex(c=0.5)
         print(json.dumps({"case": "quench", "L": args.L, "mcs": args.mcs, "B": int(rec[0, 2]),
@@ -593,8 +597,9 @@ def main():
     corr_tops = corr_ops / meas_avg_s / 1e12
     kname = {1: "k_sweep_word", 2: "k_sweep_zmarch", 3: "k_sweep_zfast", 4: "k_sweep_zdeep"}[tuned["variant"]]
     # DRAM bytes per launch from one ncu capture of the same kernel at L=2048 (sweep t=2);
-    # only quoted for the kernel that capture measured
-    traffic = {3: 1.599e9}.get(tuned["variant"]) if L == 2048 else None
+    # only quoted for the kernels those captures measured (k_sweep_zfast, 32-plane tiles;
+    # k_sweep_zdeep, 32-plane tiles, depth 3)
+    traffic = {3: 1.599e9, 4: 1.5967e9}.get(tuned["variant"]) if L == 2048 else None
     roof_sweep = {"kernel": kname + " (half-sweep)", "bound": "hbm", "achieved": sweep_gbs,
                   "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": sweep_gbs / pk["hbm_gbs"], "traffic": traffic,
                   "peak_src": pk["src"], "avg_launch_ms": sweep_avg_s * 1e3, "bytes_per_launch": bytes_per_launch,
