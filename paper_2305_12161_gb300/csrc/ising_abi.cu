@@ -28,6 +28,7 @@ struct ising_ctx {
     int64_t *rec_dev = nullptr;  // R records
     double *der_dev = nullptr;   // R x 4
     uint32_t *xt = nullptr;      // tensor-core correlation: bit-transposed lattice (lazy)
+    int *dev_err = nullptr;      // set by a device-side bounded wait that gave up
     int64_t t = 0;
     int poisoned = 0;
     int64_t launches = 0;
@@ -161,6 +162,7 @@ int ising_destroy(ising_ctx *c)
             if (c->plain) cudaFreeAsync(c->plain, c->stream);
             if (c->rec_dev) cudaFreeAsync(c->rec_dev, c->stream);
             if (c->der_dev) cudaFreeAsync(c->der_dev, c->stream);
+            if (c->dev_err) cudaFreeAsync(c->dev_err, c->stream);
             if (c->xt) cudaFreeAsync(c->xt, c->stream);
             radial_plans_destroy(c->radial, c->stream);
             c->radial = nullptr;
@@ -246,6 +248,8 @@ int ising_create_ex(ising_ctx **out, int L, int R, uint64_t seed, const ising_op
         return bail(ISING_ENOMEM);
     if (cudaMallocAsync((void **)&c->der_dev, sizeof(double) * 4 * (size_t)R, c->stream) != cudaSuccess)
         return bail(ISING_ENOMEM);
+    if (cudaMallocAsync((void **)&c->dev_err, sizeof(int) * 4, c->stream) != cudaSuccess) return bail(ISING_ENOMEM);
+    if (cudaMemsetAsync(c->dev_err, 0, sizeof(int) * 4, c->stream) != cudaSuccess) return bail(ISING_ECUDA);
     cudaError_t e;
     if (o.form == ISING_FORM_PLAIN) {
         e = launch_init_plain(c->plain, L, R, seed, c->stream);
@@ -318,6 +322,18 @@ int ising_sweep(ising_ctx *c, int64_t n)
                                  &c->launches);
     if (e != cudaSuccess) return cuda_fail(c, e, "sweep launch");
     c->t += n;
+    return ISING_OK;
+}
+
+// Synchronise the context's stream and report a device-side wait that gave up (the
+// tensor-core correlation's bounded mbarrier waits) as ISING_ETIMEOUT, which poisons the
+// context.
+static int check_device_waits(ising_ctx *c)
+{
+    int h = 0;
+    CK(c, cudaMemcpyAsync(&h, c->dev_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    if (h) return fail(c, ISING_ETIMEOUT, "tensor-core correlation: a bounded device-side wait gave up");
     return ISING_OK;
 }
 
@@ -417,7 +433,7 @@ int ising_measure_ex(ising_ctx *c, int64_t *rec, double *derived, double cval, u
             return fail(c, ISING_ENOMEM, "correlation scratch");
         }
     }
-    CK(c, launch_measure(c->lat, c->L, c->R, c->t, method, rdst, c->stream, &c->launches, c->xt));
+    CK(c, launch_measure(c->lat, c->L, c->R, c->t, method, rdst, c->stream, &c->launches, c->xt, c->dev_err));
     double *ddst = nullptr;
     if (derived) {
         ddst = dev ? derived : c->der_dev;
@@ -428,7 +444,7 @@ int ising_measure_ex(ising_ctx *c, int64_t *rec, double *derived, double cval, u
         if (rec) CK(c, cudaMemcpyAsync(rec, rdst, sizeof(int64_t) * RL * c->R, cudaMemcpyDeviceToHost, c->stream));
         if (derived)
             CK(c, cudaMemcpyAsync(derived, ddst, sizeof(double) * 4 * c->R, cudaMemcpyDeviceToHost, c->stream));
-        CK(c, cudaStreamSynchronize(c->stream));
+        return check_device_waits(c);
     }
     return ISING_OK;
 }
@@ -552,8 +568,7 @@ int ising_sync(ising_ctx *c)
     int s = check_ctx(c);
     if (s) return s;
     DeviceGuard dg(c->device);
-    CK(c, cudaStreamSynchronize(c->stream));
-    return ISING_OK;
+    return check_device_waits(c);
 }
 
 int ising_tune_sweep(int L, int replicas, int probe_mcs, const ising_opts *base, ising_opts *best,

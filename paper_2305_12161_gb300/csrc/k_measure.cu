@@ -338,7 +338,7 @@ static cudaError_t launch_corr(const uint32_t *lat, const Geom &g, int R, int64_
 }
 
 cudaError_t launch_measure(const uint32_t *lat, int L, int R, int64_t t, int corr, int64_t *rec, cudaStream_t s,
-                           int64_t *launches, uint32_t *xt_scratch)
+                           int64_t *launches, uint32_t *xt_scratch, int *err)
 {
     const Geom g = make_geom(L);
     const int64_t RL = 3 + 3 * (int64_t)(L / 2 + 1);
@@ -350,8 +350,8 @@ cudaError_t launch_measure(const uint32_t *lat, int L, int R, int64_t t, int cor
     k_mb<<<dim3((unsigned)mb, (unsigned)R), 256, 0, s>>>(lat, g, rec);
     int n = 2;
     if (corr == CORR_TENSOR) {
-        if (!xt_scratch || !corr_mma_supported(L)) return cudaErrorInvalidValue;
-        const cudaError_t e = launch_corr_mma(lat, L, R, rec, xt_scratch, s, nullptr);
+        if (!xt_scratch || !err || !corr_mma_supported(L)) return cudaErrorInvalidValue;
+        const cudaError_t e = launch_corr_mma(lat, L, R, rec, xt_scratch, err, s, nullptr);
         if (e != cudaSuccess) return e;
         n += 2;
     } else if (corr) {
