@@ -88,12 +88,13 @@ typedef struct {
 
 /* Method of the correlation sums (identical results).  POPCOUNT: XOR + bit counts over
  * packed words, any L.  TENSOR: D_a(r) = N/2 - (1/2) sum_j G[j][j+r] with G the Gram
- * matrix of the L positions over the L^2 lines of the axis, computed by fp8 warp-level
- * tensor-core MMAs on +-1 (exact: |G| <= L^2 <= 2^24 in fp32); L a multiple of 128 in
- * 256..2048; it allocates a scratch of replicas * L^3/8 bytes (the bit-transposed
- * lattice) at its first use.  AUTO: POPCOUNT (measured faster on GB300: the warp-level
- * fp8 MMA sustains about 360 TFLOP/s there, which caps the Gram path near the bit-count
- * path's speed). */
+ * matrix of the L positions over the L^2 lines of the axis, computed on the 5th-generation
+ * tensor cores (tcgen05.mma, e4m3 operands loaded by TMA, fp32 accumulators in tensor memory;
+ * exact: |G| <= L^2 <= 2^24); L a multiple of 128 in 256..2048; it allocates a scratch of
+ * replicas * L^3/8 + L^3 bytes (the bit-transposed lattice and one axis expanded to e4m3:
+ * 9.6 GB at L=2048) at its first use and keeps it (ising_release_scratch frees it).  AUTO:
+ * TENSOR for L >= 512 where it is supported and its scratch can be allocated (measured on
+ * GB300: 1.9x faster than POPCOUNT at L=512, 3.5x at L=2048; slower at L=256), else POPCOUNT. */
 typedef enum { ISING_CORR_AUTO = 0, ISING_CORR_POPCOUNT = 1, ISING_CORR_TENSOR = 2 } ising_corr;
 
 /* Sublattice order of a sweep.  01: red (q = 0) then blue every sweep (the paper's main

@@ -29,6 +29,7 @@ struct ising_ctx {
     double *der_dev = nullptr;   // R x 4
     uint32_t *xt = nullptr;      // tensor-core correlation: bit-transposed lattice (lazy)
     int *dev_err = nullptr;      // set by a device-side bounded wait that gave up
+    int xt_refused = 0;          // the tensor-core scratch could not be allocated (AUTO falls back)
     int64_t t = 0;
     int poisoned = 0;
     int64_t launches = 0;
@@ -424,13 +425,18 @@ int ising_measure_ex(ising_ctx *c, int64_t *rec, double *derived, double cval, u
     int method = CORR_NONE;
     if (corr) {
         method = CORR_POPCOUNT;
-        if (c->opts.corr == ISING_CORR_TENSOR) method = CORR_TENSOR;
+        if (c->opts.corr == ISING_CORR_TENSOR ||
+            (c->opts.corr == ISING_CORR_AUTO && c->L >= 512 && corr_mma_supported(c->L) && !c->xt_refused))
+            method = CORR_TENSOR;
     }
     if (method == CORR_TENSOR && !c->xt) {
-        const size_t bytes = (size_t)c->R * (size_t)c->L * c->L * c->L / 8;
+        const size_t bytes = corr_mma_scratch_bytes(c->L, c->R);
         if (cudaMallocAsync((void **)&c->xt, bytes, c->stream) != cudaSuccess) {
             c->xt = nullptr;
-            return fail(c, ISING_ENOMEM, "correlation scratch");
+            cudaGetLastError();  // a failed allocation is not sticky
+            if (c->opts.corr == ISING_CORR_TENSOR) return fail(c, ISING_ENOMEM, "correlation scratch");
+            c->xt_refused = 1;   // automatic choice: the bit-count path needs no scratch
+            method = CORR_POPCOUNT;
         }
     }
     CK(c, launch_measure(c->lat, c->L, c->R, c->t, method, rdst, c->stream, &c->launches, c->xt, c->dev_err));

@@ -9,18 +9,22 @@
 // integer of magnitude <= L^2 <= 2^24, so the result is exact.
 //
 // Only the upper block triangle of G is computed (G is symmetric); an entry of an
-// off-diagonal tile stands for both ordered pairs (j, k) and (k, j).  The 128 x 128 tiles are
-// accumulated by tcgen05.mma in tensor memory (kernel below); each entry's -G/2 is added to D
-// at its cyclic distance; the records start from N/2.
+// off-diagonal tile stands for both ordered pairs (j, k) and (k, j).  Per replica and axis:
+// the axis's lines are expanded once into e4m3 rows (k_expand_e4m3), and k_gram_tma
+// accumulates the 128 x 128 tiles of G by tcgen05.mma in tensor memory from TMA-loaded,
+// 128-byte swizzled shared-memory operands; each entry's -G/2 is added to D at its cyclic
+// distance; the records start from N/2.
+#include <cuda.h>
+
 #include "common.cuh"
 #include "kernels.h"
 
 namespace ising {
 
 constexpr int TM_T = 128;        // positions per tile side (M = N = 128)
-constexpr int UM_NP = 8;         // columns (K = 32 lines each) per panel, a multiple of 4
-constexpr int UM_PD = 6;         // packed panels in flight (ring slots)
-constexpr int TM_THREADS = 256;  // 8 warps: staging and expansion; warp w reads TMEM lane quarter w % 4
+constexpr int GT_STAGES = 6;     // TMA pipeline depth (32 KB per stage)
+constexpr int GT_KB = 128;       // K bytes (= lines) per stage and operand box
+constexpr int GT_STAGE_BYTES = 2 * TM_T * GT_KB;
 constexpr int UMMA_WAIT_LIMIT = 1 << 22;  // try_wait rounds before a wait gives up
 
 // x-axis columns: bundle B = rows 32B .. 32B+31 (row = y + L z); XT[B*L + x] has bit i =
@@ -61,12 +65,6 @@ __device__ __forceinline__ uint32_t e4m3x4(uint32_t n)
     return ((n * 0x10204080u) & 0x80808080u) ^ 0xB8B8B8B8u;
 }
 
-__device__ __forceinline__ void cp_async4(void *smem, const void *gmem)
-{
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 // Shared-memory matrix descriptor of tcgen05.mma for a K-major operand in 128-byte swizzled
@@ -98,49 +96,112 @@ __device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity)
     return false;
 }
 
-// Work of one replica: the three axes x npairs tile pairs (bj <= bk) x npan panels of NP
-// columns (K = 32 lines each).  Persistent CTAs take equal contiguous shares of that list; a
-// share is cut into segments that stay within one tile pair, each accumulated in a
-// 128-column fp32 tile of tensor memory and then added to S(r) of its axis.
-//
-// Per panel the packed words (staged by cp.async, two panels ahead) are expanded by all
-// threads into e4m3 operands in K-major 128-byte swizzled atoms (the swizzle keeps both the
-// expansion's stores and the tensor core's reads free of bank conflicts), and one thread
-// issues NP tcgen05.mma; tcgen05.commit on the stage's mbarrier frees
-// the operand stage for the panel after next.  Waits are made by thread 0 and shared through
-// the block, so every thread takes the same path; a wait that gives up sets *err and the CTA
-// stops after releasing its tensor memory.
-template <int NP, int PD>
-__global__ void __launch_bounds__(TM_THREADS, 1) k_corr_umma(const uint32_t *lat, const uint32_t *XT, Geom g, int nb,
-                                                              int npairs, int64_t *rec, int *err)
+// ---------------------------------------------------------------------------------
+// The Gram products run on operands expanded once per measurement: E holds, for every
+// position p of the axis and every line K of it, the e4m3 value of s (+1 -> 0x38, -1 -> 0xB8),
+// chunk-major: the 128 lines of chunk K/128 of all L positions are one block of L x 128 bytes,
+// E[(K / 128) * L * 128 + p * 128 + K % 128], so a box of 128 positions x 128 lines is 16
+// contiguous KB (rows L^2 bytes apart would put every box's rows at a large power-of-two
+// stride).  Column cc of the panels (32 lines) is K = 32 cc .. 32 cc + 31.  Every word of the
+// lattice is expanded once instead of once per tile pair.
+__global__ void k_expand_e4m3(const uint32_t *S0, const uint32_t *S1, const uint32_t *XT, Geom g, int axis,
+                              uint8_t *E)
 {
-    extern __shared__ __align__(1024) uint8_t usm[];
-    uint8_t *op = usm;  // [2 stages][A, B][NP/4 column groups][16 atoms of 8 rows x 128 B]
-    uint32_t *panel = reinterpret_cast<uint32_t *>(usm + 2 * NP * 2 * 4096);       // [PD][NP][256]
-    long long *sacc = reinterpret_cast<long long *>(panel + PD * NP * 2 * TM_T);   // S(r), r <= L/2
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(sacc + 1026);                    // [2]
-    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(mbar + 2);
+    const int L = g.L, W = g.W;
+    const int64_t ncols = (int64_t)L * L / 32;
+    const int64_t total = ncols * L;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t cc;
+        int p;
+        uint32_t v;
+        if (axis == 0) {  // XT rows are contiguous in position: consecutive threads, consecutive p
+            cc = e / L;
+            p = (int)(e - cc * L);
+            v = __ldg(XT + cc * L + p);
+        } else {          // consecutive threads, consecutive columns: consecutive words of a row
+            p = (int)(e / ncols);
+            cc = e - (int64_t)p * ncols;
+            const int pi = (int)(cc / ((int64_t)L * W));
+            const int rem = (int)(cc - (int64_t)pi * L * W);
+            const int a = rem / W;
+            const int kw = rem - a * W;
+            const int y = axis == 1 ? p : a, z = axis == 1 ? a : p;
+            v = __ldg((((pi + y + z) & 1) ? S1 : S0) + ((int64_t)z * L + y) * W + kw);
+        }
+        uint4 lo, hi;
+        lo.x = e4m3x4(v & 0xFu);
+        lo.y = e4m3x4((v >> 4) & 0xFu);
+        lo.z = e4m3x4((v >> 8) & 0xFu);
+        lo.w = e4m3x4((v >> 12) & 0xFu);
+        hi.x = e4m3x4((v >> 16) & 0xFu);
+        hi.y = e4m3x4((v >> 20) & 0xFu);
+        hi.z = e4m3x4((v >> 24) & 0xFu);
+        hi.w = e4m3x4(v >> 28);
+        uint4 *dst = reinterpret_cast<uint4 *>(E + (cc >> 2) * ((int64_t)L * GT_KB) + (int64_t)p * GT_KB + 32 * (cc & 3));
+        dst[0] = lo;
+        dst[1] = hi;
+    }
+}
+
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t addr, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(addr), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *tm, int x, int y, uint32_t mbar)
+{
+    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+                 ::"r"(dst), "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(mbar)
+                 : "memory");
+}
+
+// One CTA per (tile pair (bj <= bk), K slice): thread 0 loads the 128 x 128-byte boxes of both
+// tiles by TMA (128-byte swizzle) into a ring of GT_STAGES stages, thread 32 issues four
+// tcgen05.mma per stage into a 128-column fp32 accumulator in tensor memory and frees the
+// stage by tcgen05.commit; then all four warps read the accumulator and add each entry's
+// -G/2 to D at its cyclic distance.  The CTAs of one K slice run together and stream the same
+// columns, so L2 serves the tiles' repeated reads.  Every wait is bounded; one that gives up
+// sets *err and the CTA stops after releasing its tensor memory.
+__global__ void __launch_bounds__(128, 1) k_gram_tma(const __grid_constant__ CUtensorMap tm, int L, int nb,
+                                                     int npairs, int split, int64_t *D, int *err)
+{
+    extern __shared__ __align__(1024) uint8_t gsm[];
+    uint8_t *stage0 = gsm;                                                   // [S][A 16 KB, B 16 KB]
+    long long *sacc = reinterpret_cast<long long *>(gsm + GT_STAGES * GT_STAGE_BYTES);
+    uint64_t *full = reinterpret_cast<uint64_t *>(sacc + 1026);
+    uint64_t *empty = full + GT_STAGES;
+    uint64_t *done = empty + GT_STAGES;
+    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(done + 1);
     int *flag = reinterpret_cast<int *>(tmem_holder + 1);
 
-    const int r = blockIdx.y;
-    const int L = g.L, H = L / 2, W = g.W;
+    const int H = L / 2;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint32_t *S0 = lat + 2 * (int64_t)r * g.nw;
-    const uint32_t *S1 = S0 + g.nw;
-    const int64_t ncols = 2 * (int64_t)L * W;  // columns per axis (x: L^2/32 bundles, the same count)
-    const int64_t npan = ncols / NP;
-    const int64_t total = 3LL * npairs * npan;
-    const int64_t w_begin = total * blockIdx.x / gridDim.x, w_end = total * (blockIdx.x + 1) / gridDim.x;
+    const int sl = blockIdx.x / npairs;
+    int p = blockIdx.x - sl * npairs;
+    int bj = 0;
+    while (p >= nb - bj) {
+        p -= nb - bj;
+        ++bj;
+    }
+    const int bk = bj + p;
+    const int j0 = bj * TM_T, k0 = bk * TM_T;
+    const int nk = (int)((int64_t)L * L / GT_KB);
+    const int c0 = (int)((int64_t)nk * sl / split), c1 = (int)((int64_t)nk * (sl + 1) / split);
+    const int n = c1 - c0;
 
-    for (int i = tid; i <= H; i += TM_THREADS) sacc[i] = 0;
+    for (int i = tid; i <= H; i += 128) sacc[i] = 0;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
                      "r"(TM_T));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])));
+        for (int i = 0; i < GT_STAGES; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[i])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[i])));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(done)));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         *flag = 1;
     }
@@ -149,124 +210,55 @@ __global__ void __launch_bounds__(TM_THREADS, 1) k_corr_umma(const uint32_t *lat
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_holder;
 
-    int gi = 0;  // panels processed by this CTA: selects the stage and the mbarrier phase
-    for (int64_t w = w_begin; w < w_end;) {
-        const int64_t unit = w / npan;  // (axis, pair)
-        const int64_t pan0 = w - unit * npan;
-        const int64_t pan1 = (w_end - w) < (npan - pan0) ? pan0 + (w_end - w) : npan;
-        const int n = (int)(pan1 - pan0);
-        w += n;
-        const int axis = (int)(unit / npairs);
-        int p = (int)(unit - (int64_t)axis * npairs);
-        int bj = 0;
-        while (p >= nb - bj) {
-            p -= nb - bj;
-            ++bj;
+    if (tid == 0) {  // producer
+        for (int t = 0; t < n; ++t) {
+            const int st = t % GT_STAGES;
+            if (t >= GT_STAGES && !mbar_wait(smem_u32(&empty[st]), (uint32_t)(((t / GT_STAGES) - 1) & 1))) {
+                *flag = 0;
+                break;
+            }
+            if (!*(volatile int *)flag) break;
+            const uint32_t sa = smem_u32(stage0 + st * GT_STAGE_BYTES);
+            mbar_expect_tx(smem_u32(&full[st]), GT_STAGE_BYTES);
+            tma_load_2d(sa, &tm, 0, (c0 + t) * L + j0, smem_u32(&full[st]));
+            tma_load_2d(sa + TM_T * GT_KB, &tm, 0, (c0 + t) * L + k0, smem_u32(&full[st]));
         }
-        const int bk = bj + p;
-        const int j0 = bj * TM_T, k0 = bk * TM_T;
-        const uint32_t *X = axis == 0 ? XT + (int64_t)r * ncols * L : nullptr;
-
-        // staging: element (c, pp) of a panel = column c, pair position pp (pp < 128: tile bj
-        // (A), else tile bk (B)); the threads take consecutive elements
-        auto issue = [&](int64_t pan, int stage) {
-            uint32_t *pl = panel + stage * NP * 2 * TM_T;
-            if (axis == 0) {  // XT rows are contiguous in position: consecutive pp
-#pragma unroll
-                for (int idx = tid; idx < NP * 2 * TM_T; idx += TM_THREADS) {
-                    const int c = idx / (2 * TM_T), pp = idx % (2 * TM_T);
-                    const int jj = pp < TM_T ? j0 + pp : k0 + (pp - TM_T);
-                    cp_async4(&pl[c * 2 * TM_T + pp], X + (pan * NP + c) * (int64_t)L + jj);
-                }
-            } else {
-                // consecutive threads take consecutive columns of one position: consecutive
-                // words of one row (coalesced); the thread's column is fixed
-                const int c = tid % NP;
-                const int cc = (int)(pan * NP) + c;
-                const int pi = cc / (L * W);
-                const int rem = cc - pi * L * W;
-                const int a = rem / W;
-                const int kw = rem - a * W;
-#pragma unroll
-                for (int idx = tid; idx < NP * 2 * TM_T; idx += TM_THREADS) {
-                    const int pp = idx / NP;
-                    const int jj = pp < TM_T ? j0 + pp : k0 + (pp - TM_T);
-                    const int y = axis == 1 ? jj : a, z = axis == 1 ? a : jj;
-                    cp_async4(&pl[c * 2 * TM_T + pp], (((pi + y + z) & 1) ? S1 : S0) + ((int64_t)z * L + y) * W + kw);
-                }
+    } else if (tid == 32) {  // MMA issuer
+        int t = 0;
+        for (; t < n; ++t) {
+            const int st = t % GT_STAGES;
+            if (!mbar_wait(smem_u32(&full[st]), (uint32_t)((t / GT_STAGES) & 1))) {
+                *flag = 0;
+                break;
             }
-            asm volatile("cp.async.commit_group;\n" ::: "memory");
-        };
-
-        // packed panels run PD ahead in a ring of their own (panel i of the segment in slot
-        // (gi0 + i) % PD); operand stages alternate with gi
-        const int gi0 = gi;
-        for (int k = 0; k < PD - 1 && k < n; ++k) issue(pan0 + k, (gi0 + k) % PD);
-        for (int i = 0; i < n; ++i, ++gi) {
-            const int st = gi & 1;
-            if (i + PD - 1 < n) issue(pan0 + i + PD - 1, (gi0 + i + PD - 1) % PD);
-            if (i + PD - 1 < n)
-                asm volatile("cp.async.wait_group %0;\n" ::"n"(PD - 1) : "memory");
-            else
-                asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-            if (gi >= 2 && tid == 0 && !mbar_wait(smem_u32(&mbar[st]), (uint32_t)(((gi - 2) >> 1) & 1))) *flag = 0;
-            __syncthreads();  // packed panel visible; operand stage st free (or the wait gave up)
-            if (!*flag) break;
-            const uint32_t *pl = panel + ((gi0 + i) % PD) * NP * 2 * TM_T;
-            uint8_t *ops = op + st * NP * 2 * 4096;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t sa = smem_u32(stage0 + st * GT_STAGE_BYTES);
 #pragma unroll
-            for (int idx = tid; idx < NP * 2 * TM_T; idx += TM_THREADS) {
-                const int c = idx / (2 * TM_T), pp = idx % (2 * TM_T);
-                const int pos = pp & (TM_T - 1), half = pp >> 7;
-                const uint32_t v = pl[c * 2 * TM_T + pp];
-                uint4 lo, hi;
-                lo.x = e4m3x4(v & 0xFu);
-                lo.y = e4m3x4((v >> 4) & 0xFu);
-                lo.z = e4m3x4((v >> 8) & 0xFu);
-                lo.w = e4m3x4((v >> 12) & 0xFu);
-                hi.x = e4m3x4((v >> 16) & 0xFu);
-                hi.y = e4m3x4((v >> 20) & 0xFu);
-                hi.z = e4m3x4((v >> 24) & 0xFu);
-                hi.w = e4m3x4(v >> 28);
-                // operand (half) of column group c/4: atom pos/8, row r = pos%8; the column's
-                // two 16-byte chunks 2(c%4) and 2(c%4)+1 of the row, swizzled by r
-                const int r8 = pos & 7, ch = 2 * (c & 3);
-                uint8_t *row = ops + (half * (NP / 4) + (c >> 2)) * 16384 + (pos >> 3) * 1024 + r8 * 128;
-                *reinterpret_cast<uint4 *>(row + ((ch ^ r8) << 4)) = lo;        // lines 0..15 of the column
-                *reinterpret_cast<uint4 *>(row + (((ch + 1) ^ r8) << 4)) = hi;  // lines 16..31
+            for (int q = 0; q < GT_KB / 32; ++q) {
+                const uint64_t ad = umma_desc_sw128(sa + 32 * q), bd = umma_desc_sw128(sa + TM_T * GT_KB + 32 * q);
+                const uint32_t acc = (t > 0 || q > 0) ? 1u : 0u;
+                asm volatile("{\n.reg .pred p;\nsetp.ne.u32 p, %4, 0;\n"
+                             "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                             "l"(ad), "l"(bd), "r"(UMMA_IDESC), "r"(acc));
             }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            __syncthreads();  // operands written; packed panel consumed
-            if (tid == 0) {
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll
-                for (int c = 0; c < NP; ++c) {
-                    const uint32_t koff = (uint32_t)((c >> 2) * 16384 + (c & 3) * 32);
-                    const uint64_t ad = umma_desc_sw128(smem_u32(ops) + koff);
-                    const uint64_t bd = umma_desc_sw128(smem_u32(ops) + (NP / 4) * 16384 + koff);
-                    const uint32_t acc = (i > 0 || c > 0) ? 1u : 0u;
-                    asm volatile("{\n.reg .pred p;\nsetp.ne.u32 p, %4, 0;\n"
-                                 "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                                 "l"(ad), "l"(bd), "r"(UMMA_IDESC), "r"(acc));
-                }
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                    smem_u32(&mbar[st])));
-            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_u32(&empty[st])));
         }
-        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-        // the segment's last commit covers every MMA issued before it
-        if (tid == 0 && *flag && !mbar_wait(smem_u32(&mbar[(gi - 1) & 1]), (uint32_t)(((gi - 1) >> 1) & 1)))
-            *flag = 0;
-        __syncthreads();
-        if (!*flag) break;
+        if (t > 0) {  // the last commit covers every MMA before it
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_u32(done)));
+            if (!mbar_wait(smem_u32(done), 0u)) *flag = 0;
+        }
+    }
+    __syncthreads();
+    const bool ok = *flag && n > 0;
+    if (ok) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const int quarter = warp & 3;            // TMEM lanes this warp may read
-        const int j = j0 + 32 * quarter + lane;  // this thread's row of the tile
-        constexpr int CPW = TM_T / (TM_THREADS / 128);  // accumulator columns per warp
+        const int j = j0 + 32 * warp + lane;  // this thread's row of the tile (TMEM lane)
 #pragma unroll 1
-        for (int c0 = (warp >> 2) * CPW; c0 < (warp >> 2) * CPW + CPW; c0 += 16) {
+        for (int cc = 0; cc < TM_T; cc += 16) {
             uint32_t v[16];
-            const uint32_t ta = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)c0;
+            const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)cc;
             asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
                          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
                            "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
@@ -275,7 +267,7 @@ __global__ void __launch_bounds__(TM_THREADS, 1) k_corr_umma(const uint32_t *lat
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
-                const int k = k0 + c0 + q;
+                const int k = k0 + cc + q;
                 const long long G = (long long)__float2int_rn(__uint_as_float(v[q]));
                 if (bj == bk) {
                     int d = k - j;
@@ -288,65 +280,94 @@ __global__ void __launch_bounds__(TM_THREADS, 1) k_corr_umma(const uint32_t *lat
                 }
             }
         }
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();  // the accumulator is read; the next segment may overwrite it
-        int64_t *D = rec + (int64_t)r * (3 + 3 * (int64_t)(H + 1)) + 3 + (int64_t)axis * (H + 1);
-        for (int i = 1 + tid; i <= H; i += TM_THREADS)
-            if (sacc[i]) {
-                atomicAdd((unsigned long long *)(D + i), (unsigned long long)(-(sacc[i] / 2)));
-                sacc[i] = 0;
-            }
-        __syncthreads();
     }
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-    if (!*flag && tid == 0) {
-        atomicExch(err, 1);
-        if (gi > 0) mbar_wait(smem_u32(&mbar[(gi - 1) & 1]), (uint32_t)(((gi - 1) >> 1) & 1));  // in-flight MMAs
-    }
+    if (!*flag && tid == 0) atomicExch(err, 1);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TM_T));
+    if (!ok) return;
+    for (int i = 1 + tid; i <= H; i += 128)
+        if (sacc[i]) atomicAdd((unsigned long long *)(D + i), (unsigned long long)(-(sacc[i] / 2)));
 }
 
-template <int NP, int PD>
-static size_t umma_smem_bytes()
+static size_t gram_smem_bytes() { return (size_t)GT_STAGES * GT_STAGE_BYTES + 1026 * 8 + (2 * GT_STAGES + 1) * 8 + 16; }
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// The driver's tensor-map encoder, looked up once through the runtime (no link to libcuda).
+static EncodeTiledFn encode_tiled()
 {
-    return (size_t)2 * NP * 2 * 4096 + (size_t)PD * NP * 2 * TM_T * 4 + 1026 * 8 + 2 * 8 + 8;
+    static EncodeTiledFn fn = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(f);
+        looked = true;
+    }
+    return fn;
 }
 
 bool corr_mma_supported(int L) { return L >= 256 && L <= 2048 && L % TM_T == 0 && L % 64 == 0; }
 
-cudaError_t launch_corr_mma(const uint32_t *lat, int L, int R, int64_t *rec, uint32_t *xt_scratch, int *err,
+size_t corr_mma_scratch_bytes(int L, int R)
+{
+    return (size_t)R * (size_t)L * L * L / 8 + (size_t)L * L * L;  // transposed lattice + expanded axis
+}
+
+cudaError_t launch_corr_mma(const uint32_t *lat, int L, int R, int64_t *rec, uint32_t *scratch, int *err,
                             cudaStream_t s, int64_t *launches)
 {
     const Geom g = make_geom(L);
+    uint32_t *XT = scratch;
+    uint8_t *E = reinterpret_cast<uint8_t *>(scratch + (size_t)R * L * L * L / 32);
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc) return cudaErrorNotSupported;
+    CUtensorMap tm;
+    // E viewed as rows of 128 bytes: row (chunk * L + position)
+    const cuuint64_t gdim[2] = {(cuuint64_t)GT_KB, (cuuint64_t)L * L * L / GT_KB};
+    const cuuint64_t gstride[1] = {(cuuint64_t)GT_KB};
+    const cuuint32_t box[2] = {GT_KB, TM_T};
+    const cuuint32_t estr[2] = {1, 1};
+    if (enc(&tm, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, E, gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
     {
         const int64_t tasks = (int64_t)L * L / 32 * 2 * g.W;
         int64_t blocks = (tasks + 7) / 8;
         if (blocks > 152 * 32) blocks = 152 * 32;
-        k_transpose_x<<<dim3((unsigned)blocks, (unsigned)R), 256, 0, s>>>(lat, g, xt_scratch);
+        k_transpose_x<<<dim3((unsigned)blocks, (unsigned)R), 256, 0, s>>>(lat, g, XT);
     }
-    constexpr int NP = UM_NP, PD = UM_PD;
-    const int nb = L / TM_T;
-    const int npairs = nb * (nb + 1) / 2;
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    const size_t smem = umma_smem_bytes<NP, PD>();
-    if ((e = cudaFuncSetAttribute(k_corr_umma<NP, PD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
-        cudaSuccess)
+    const size_t smem = gram_smem_bytes();
+    if ((e = cudaFuncSetAttribute(k_gram_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
         return e;
-    int occ = 1;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_corr_umma<NP, PD>, TM_THREADS, smem)) != cudaSuccess)
-        return e;
-    if (occ < 1) occ = 1;
-    // persistent: one wave of CTAs shares the replicas' work equally
-    int ctas = (int)(((int64_t)occ * sms + R - 1) / R);
-    if (ctas < 1) ctas = 1;
-    k_corr_umma<NP, PD><<<dim3((unsigned)ctas, (unsigned)R), TM_THREADS, smem, s>>>(lat, xt_scratch, g, nb, npairs, rec,
-                                                                                err);
-    if (launches) *launches += 2;
+    const int nb = L / TM_T;
+    const int npairs = nb * (nb + 1) / 2;
+    int split = sms / npairs;  // one CTA per SM: K slices x tile pairs <= SMs
+    if (split < 1) split = 1;
+    const int64_t H = L / 2, RL = 3 + 3 * (H + 1);
+    int64_t nl = 1;
+    for (int r = 0; r < R; ++r) {
+        const uint32_t *S0 = lat + 2 * (int64_t)r * g.nw;
+        for (int axis = 0; axis < 3; ++axis) {
+            k_expand_e4m3<<<(unsigned)(sms * 8), 256, 0, s>>>(S0, S0 + g.nw, XT + (int64_t)r * L * L * L / 32, g,
+                                                             axis, E);
+            k_gram_tma<<<(unsigned)(npairs * split), 128, smem, s>>>(tm, L, nb, npairs, split,
+                                                                     rec + r * RL + 3 + axis * (H + 1), err);
+            nl += 2;
+        }
+    }
+    if (launches) *launches += nl;
     return cudaGetLastError();
 }
 

@@ -92,13 +92,14 @@ cudaError_t launch_unpack(const uint32_t *lat, int8_t *plain, int L, int R, cuda
 // ---- measurement on the packed store ----------------------------------------------
 // rec: R records of 3 + 3*(L/2+1) int64 (must not alias lat).  Writes t, M, B and the
 // correlation sums D_a(r) by the chosen method (CORR_NONE writes D_a(r) = -1).
-// CORR_TENSOR needs corr_mma_supported(L), xt_scratch of R * L^3 / 8 bytes and err (a device
-// int set to 1 if a bounded wait of the tensor-core kernel gave up; the records are then
-// incomplete).
+// CORR_TENSOR needs corr_mma_supported(L), xt_scratch of corr_mma_scratch_bytes(L, R) bytes
+// and err (a device int set to 1 if a bounded wait of the tensor-core kernel gave up; the
+// records are then incomplete).
 enum CorrMethod : int { CORR_NONE = 0, CORR_POPCOUNT = 1, CORR_TENSOR = 2 };
 cudaError_t launch_measure(const uint32_t *lat, int L, int R, int64_t t, int corr, int64_t *rec,
                            cudaStream_t s, int64_t *launches, uint32_t *xt_scratch = nullptr, int *err = nullptr);
 bool corr_mma_supported(int L);
+size_t corr_mma_scratch_bytes(int L, int R);
 cudaError_t launch_corr_mma(const uint32_t *lat, int L, int R, int64_t *rec, uint32_t *xt_scratch, int *err,
                             cudaStream_t s, int64_t *launches);
 // derived: R x [e, m, l_E, l_C]
