@@ -22,9 +22,10 @@
 namespace ising {
 
 constexpr int TM_T = 128;        // positions per tile side (M = N = 128)
-constexpr int GT_STAGES = 6;     // TMA pipeline depth (32 KB per stage)
+constexpr int GT_N = 256;        // B rows per CTA: two adjacent 128-position tiles (MMA N = 256)
+constexpr int GT_STAGES = 4;     // TMA pipeline depth (48 KB per stage)
 constexpr int GT_KB = 128;       // K bytes (= lines) per stage and operand box
-constexpr int GT_STAGE_BYTES = 2 * TM_T * GT_KB;
+constexpr int GT_STAGE_BYTES = (TM_T + GT_N) * GT_KB;
 constexpr int UMMA_WAIT_LIMIT = 1 << 22;  // try_wait rounds before a wait gives up
 
 // x-axis columns: bundle B = rows 32B .. 32B+31 (row = y + L z); XT[B*L + x] has bit i =
@@ -78,8 +79,8 @@ __device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr)
            ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
-// Instruction descriptor: D in f32, A and B e4m3, both K-major, M = 128, N = 128.
-constexpr uint32_t UMMA_IDESC = (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(TM_T >> 3) << 17) |
+// Instruction descriptor: D in f32, A and B e4m3, both K-major, M = 128, N = GT_N.
+constexpr uint32_t UMMA_IDESC = (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(GT_N >> 3) << 17) |
                                 ((uint32_t)(TM_T >> 4) << 24);
 
 // Bounded wait for phase `parity` of an mbarrier; false when it gave up.
@@ -156,18 +157,21 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *tm,
                  : "memory");
 }
 
-// One CTA per (tile pair (bj <= bk), K slice): thread 0 loads the 128 x 128-byte boxes of both
-// tiles by TMA (128-byte swizzle) into a ring of GT_STAGES stages, thread 32 issues four
-// tcgen05.mma per stage into a 128-column fp32 accumulator in tensor memory and frees the
-// stage by tcgen05.commit; then all four warps read the accumulator and add each entry's
-// -G/2 to D at its cyclic distance.  The CTAs of one K slice run together and stream the same
-// columns, so L2 serves the tiles' repeated reads.  Every wait is bounded; one that gives up
-// sets *err and the CTA stops after releasing its tensor memory.
-__global__ void __launch_bounds__(128, 1) k_gram_tma(const __grid_constant__ CUtensorMap tm, int L, int nb,
-                                                     int npairs, int split, int64_t *D, int *err)
+// One CTA per (tile bj, super-tile sb of columns 2 sb, 2 sb + 1, K slice), 2 sb + 1 >= bj: thread
+// 0 loads the 128 x 128-byte box of tile bj and the 256 x 128-byte box of the super-tile by TMA
+// (128-byte swizzle) into a ring of GT_STAGES stages, thread 32 issues four tcgen05.mma of
+// 128 x 256 x 32 per stage into a 256-column fp32 accumulator in tensor memory and frees the
+// stage by tcgen05.commit; then all four warps read the accumulator and add each entry of an
+// upper-triangle tile (bk >= bj, bk < nb) as -G/2 to D at its cyclic distance.  The CTAs of
+// one K slice run together and stream the same columns, so L2 serves the tiles' repeated
+// reads.  Every wait is bounded; one that gives up sets *err and the CTA stops after releasing
+// its tensor memory.
+__global__ void __launch_bounds__(128, 1) k_gram_tma(const __grid_constant__ CUtensorMap tmA,
+                                                     const __grid_constant__ CUtensorMap tmB, int L, int nb,
+                                                     int nunits, int split, int64_t *D, int *err)
 {
     extern __shared__ __align__(1024) uint8_t gsm[];
-    uint8_t *stage0 = gsm;                                                   // [S][A 16 KB, B 16 KB]
+    uint8_t *stage0 = gsm;  // [S][A 16 KB, B 32 KB]
     long long *sacc = reinterpret_cast<long long *>(gsm + GT_STAGES * GT_STAGE_BYTES);
     uint64_t *full = reinterpret_cast<uint64_t *>(sacc + 1026);
     uint64_t *empty = full + GT_STAGES;
@@ -177,15 +181,16 @@ __global__ void __launch_bounds__(128, 1) k_gram_tma(const __grid_constant__ CUt
 
     const int H = L / 2;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int sl = blockIdx.x / npairs;
-    int p = blockIdx.x - sl * npairs;
+    const int sl = blockIdx.x / nunits;
+    int u = blockIdx.x - sl * nunits;
+    const int nsb = (nb + 1) / 2;
     int bj = 0;
-    while (p >= nb - bj) {
-        p -= nb - bj;
+    while (u >= nsb - bj / 2) {
+        u -= nsb - bj / 2;
         ++bj;
     }
-    const int bk = bj + p;
-    const int j0 = bj * TM_T, k0 = bk * TM_T;
+    const int sb = bj / 2 + u;
+    const int j0 = bj * TM_T, s0 = sb * GT_N;
     const int nk = (int)((int64_t)L * L / GT_KB);
     const int c0 = (int)((int64_t)nk * sl / split), c1 = (int)((int64_t)nk * (sl + 1) / split);
     const int n = c1 - c0;
@@ -193,7 +198,7 @@ __global__ void __launch_bounds__(128, 1) k_gram_tma(const __grid_constant__ CUt
     for (int i = tid; i <= H; i += 128) sacc[i] = 0;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
-                     "r"(TM_T));
+                     "r"(GT_N));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
@@ -220,8 +225,8 @@ __global__ void __launch_bounds__(128, 1) k_gram_tma(const __grid_constant__ CUt
             if (!*(volatile int *)flag) break;
             const uint32_t sa = smem_u32(stage0 + st * GT_STAGE_BYTES);
             mbar_expect_tx(smem_u32(&full[st]), GT_STAGE_BYTES);
-            tma_load_2d(sa, &tm, 0, (c0 + t) * L + j0, smem_u32(&full[st]));
-            tma_load_2d(sa + TM_T * GT_KB, &tm, 0, (c0 + t) * L + k0, smem_u32(&full[st]));
+            tma_load_2d(sa, &tmA, 0, (c0 + t) * L + j0, smem_u32(&full[st]));
+            tma_load_2d(sa + TM_T * GT_KB, &tmB, 0, (c0 + t) * L + s0, smem_u32(&full[st]));
         }
     } else if (tid == 32) {  // MMA issuer
         int t = 0;
@@ -256,7 +261,9 @@ __global__ void __launch_bounds__(128, 1) k_gram_tma(const __grid_constant__ CUt
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const int j = j0 + 32 * warp + lane;  // this thread's row of the tile (TMEM lane)
 #pragma unroll 1
-        for (int cc = 0; cc < TM_T; cc += 16) {
+        for (int cc = 0; cc < GT_N; cc += 16) {
+            const int bk = 2 * sb + cc / TM_T;
+            if (bk < bj || bk >= nb) continue;  // lower-triangle or missing tile of the super-tile
             uint32_t v[16];
             const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)cc;
             asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
@@ -267,7 +274,7 @@ __global__ void __launch_bounds__(128, 1) k_gram_tma(const __grid_constant__ CUt
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
-                const int k = k0 + cc + q;
+                const int k = s0 + cc + q;
                 const long long G = (long long)__float2int_rn(__uint_as_float(v[q]));
                 if (bj == bk) {
                     int d = k - j;
@@ -284,7 +291,7 @@ __global__ void __launch_bounds__(128, 1) k_gram_tma(const __grid_constant__ CUt
     if (!*flag && tid == 0) atomicExch(err, 1);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TM_T));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(GT_N));
     if (!ok) return;
     for (int i = 1 + tid; i <= H; i += 128)
         if (sacc[i]) atomicAdd((unsigned long long *)(D + i), (unsigned long long)(-(sacc[i] / 2)));
@@ -328,13 +335,16 @@ cudaError_t launch_corr_mma(const uint32_t *lat, int L, int R, int64_t *rec, uin
     uint8_t *E = reinterpret_cast<uint8_t *>(scratch + (size_t)R * L * L * L / 32);
     EncodeTiledFn enc = encode_tiled();
     if (!enc) return cudaErrorNotSupported;
-    CUtensorMap tm;
-    // E viewed as rows of 128 bytes: row (chunk * L + position)
+    // E viewed as rows of 128 bytes: row (chunk * L + position); boxes of 128 and 256 rows
+    CUtensorMap tmA, tmB;
     const cuuint64_t gdim[2] = {(cuuint64_t)GT_KB, (cuuint64_t)L * L * L / GT_KB};
     const cuuint64_t gstride[1] = {(cuuint64_t)GT_KB};
-    const cuuint32_t box[2] = {GT_KB, TM_T};
+    const cuuint32_t boxA[2] = {GT_KB, TM_T}, boxB[2] = {GT_KB, GT_N};
     const cuuint32_t estr[2] = {1, 1};
-    if (enc(&tm, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, E, gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+    if (enc(&tmA, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, E, gdim, gstride, boxA, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS ||
+        enc(&tmB, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, E, gdim, gstride, boxB, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
@@ -351,9 +361,10 @@ cudaError_t launch_corr_mma(const uint32_t *lat, int L, int R, int64_t *rec, uin
     const size_t smem = gram_smem_bytes();
     if ((e = cudaFuncSetAttribute(k_gram_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
         return e;
-    const int nb = L / TM_T;
-    const int npairs = nb * (nb + 1) / 2;
-    int split = sms / npairs;  // one CTA per SM: K slices x tile pairs <= SMs
+    const int nb = L / TM_T, nsb = (nb + 1) / 2;
+    int nunits = 0;  // (tile row bj, super-tile sb >= bj / 2)
+    for (int bj = 0; bj < nb; ++bj) nunits += nsb - bj / 2;
+    int split = sms / nunits;  // one CTA per SM: K slices x units <= SMs
     if (split < 1) split = 1;
     const int64_t H = L / 2, RL = 3 + 3 * (H + 1);
     int64_t nl = 1;
@@ -362,7 +373,7 @@ cudaError_t launch_corr_mma(const uint32_t *lat, int L, int R, int64_t *rec, uin
         for (int axis = 0; axis < 3; ++axis) {
             k_expand_e4m3<<<(unsigned)(sms * 8), 256, 0, s>>>(S0, S0 + g.nw, XT + (int64_t)r * L * L * L / 32, g,
                                                              axis, E);
-            k_gram_tma<<<(unsigned)(npairs * split), 128, smem, s>>>(tm, L, nb, npairs, split,
+            k_gram_tma<<<(unsigned)(nunits * split), 128, smem, s>>>(tmA, tmB, L, nb, nunits, split,
                                                                      rec + r * RL + 3 + axis * (H + 1), err);
             nl += 2;
         }
