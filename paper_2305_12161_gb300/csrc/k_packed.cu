@@ -215,17 +215,20 @@ __global__ void __launch_bounds__(1024) k_sweep_zmarch(uint32_t *lat, Geom g, in
 // compile-time.  Per plane each thread reads one new other-sublattice word of its own
 // column (z+1) and keeps z-1 and z in registers; the y-neighbours and the x edge come
 // from the shared ring; its own-sublattice word is prefetched from global memory two
-// planes ahead into registers.  Philox round keys are computed once per thread.
+// planes ahead into registers.  Philox round keys are computed once per thread.  The rows
+// a warp computes share their parity, so the direction of the x-neighbour shift (which
+// alternates with y + z) is the same for the whole warp; own-word pointer and Philox
+// counter advance by one plane per step.
 template <int RULE, int W4>
 __global__ void __launch_bounds__(256) k_sweep_zfast(uint32_t *lat, Geom g, int q, uint32_t t, uint64_t seed, int TZ)
 {
     constexpr int NT = 256, TY = NT / W4;
     constexpr int OSZ = (TY + 2) * W4;  // uint4 per ring slot: the tile and one halo row each side
     constexpr int NS = 5;               // slots: planes z, z+1 being read, z+2, z+3 in flight, 1 spare
+    constexpr int RW = 32 / W4;         // rows per warp
     __shared__ uint4 ring[NS * OSZ];
     const int L = g.L;
     const int tid = threadIdx.x;
-    const int ty = tid / W4, cx = tid % W4;
     const int nty = L / TY;
     const int y0 = (int)(blockIdx.x % nty) * TY;
     const int z0 = (int)(blockIdx.x / nty) * TZ;
@@ -235,15 +238,22 @@ __global__ void __launch_bounds__(256) k_sweep_zfast(uint32_t *lat, Geom g, int 
     const PhiloxKeys keys = philox_keys(seed + (uint64_t)r);
     const int64_t plane4 = (int64_t)L * W4;
 
-    // copy sources of this thread inside a plane: ring row ty <- global row y0-1+ty, and
-    // for tid < 2*W4 ring row TY+tid/W4 <- global row y0-1+TY+tid/W4
-    int ya = y0 - 1 + ty;
+    // copies: thread tid fills ring row tid / W4 (global row y0-1+tid/W4) and, for
+    // tid < 2*W4, ring row TY + tid/W4
+    const int ly = tid / W4, lx = tid % W4;
+    int ya = y0 - 1 + ly;
     ya = ya < 0 ? ya + L : ya;
-    const int64_t offa = (int64_t)ya * W4 + cx;
+    const int64_t offa = (int64_t)ya * W4 + lx;
     const bool halo = tid < 2 * W4;
-    int yb = y0 - 1 + TY + ty;  // ty is 0 or 1 here
+    int yb = y0 - 1 + TY + ly;  // ly is 0 or 1 here
     yb = yb >= L ? yb - L : yb;
-    const int64_t offb = (int64_t)yb * W4 + cx;
+    const int64_t offb = (int64_t)yb * W4 + lx;
+
+    // compute: the rows of a warp share their parity, so the x-neighbour direction (which
+    // alternates with y + z) is uniform across the warp
+    const int warp = tid >> 5, lane = tid & 31;
+    const int cx = lane % W4;
+    const int ty = (warp >> 1) * 2 * RW + (warp & 1) + 2 * (lane / W4);
     const int y = y0 + ty;
     const int64_t own = (int64_t)y * W4 + cx;  // own column within a plane
 
@@ -261,20 +271,23 @@ __global__ void __launch_bounds__(256) k_sweep_zfast(uint32_t *lat, Geom g, int 
 
 #pragma unroll 1
     for (int gi = 0; gi < 4; ++gi) issue(gi);
-    uint4 sA = S4[(int64_t)z0 * plane4 + own];
-    uint4 sB = TZ > 1 ? S4[(int64_t)(z0 + 1) * plane4 + own] : sA;
+    uint4 *sp = S4 + (int64_t)z0 * plane4 + own;  // own word at plane z
+    uint4 sA = sp[0];
+    uint4 sB = TZ > 1 ? sp[plane4] : sA;
     cp_async_wait<2>();  // groups 0 and 1 (planes z0-1, z0) have landed
     __syncthreads();
     uint4 cm = ring[0 * OSZ + (ty + 1) * W4 + cx];  // plane z-1, own column
     uint4 cc = ring[1 * OSZ + (ty + 1) * W4 + cx];  // plane z
     const int cxl = (cx + W4 - 1) % W4, cxr = (cx + 1) % W4;
     int sz = 1;  // slot of plane z
-#pragma unroll 1
+    int p = (y + z0 + q) & 1;
+    uint32_t gidx = (uint32_t)((int64_t)z0 * plane4 + own);  // Philox group = word >> 2
+    const uint32_t gstep = (uint32_t)plane4;
+#pragma unroll 1  // unrolling by two measured 5% slower
     for (int i = 0; i < TZ; ++i) {
         cp_async_wait<1>();  // group i+2 (plane z+1) has landed
         __syncthreads();
         issue(i + 4);        // overwrites the slot of plane z-2, last read in step i-1
-        const int z = z0 + i;
         const int szp = sz == NS - 1 ? 0 : sz + 1;
         const uint4 *Oz = ring + sz * OSZ;
         const uint4 cp = ring[szp * OSZ + (ty + 1) * W4 + cx];
@@ -282,8 +295,7 @@ __global__ void __launch_bounds__(256) k_sweep_zfast(uint32_t *lat, Geom g, int 
         const uint4 yp = Oz[(ty + 2) * W4 + cx];
         const uint4 s = sA;
         sA = sB;
-        if (i + 2 < TZ) sB = S4[(int64_t)(z + 2) * plane4 + own];
-        const int p = (y + z + q) & 1;
+        if (i + 2 < TZ) sB = sp[2 * plane4];
         uint4 X;
         if (p == 0) {
             const uint32_t e = Oz[(ty + 1) * W4 + cxl].w;
@@ -303,7 +315,6 @@ __global__ void __launch_bounds__(256) k_sweep_zfast(uint32_t *lat, Geom g, int 
         count6(cc.y, X.y, ym.y, yp.y, cm.y, cp.y, g1, e1);
         count6(cc.z, X.z, ym.z, yp.z, cm.z, cp.z, g2, e2);
         count6(cc.w, X.w, ym.w, yp.w, cm.w, cp.w, g3, e3);
-        const uint32_t gidx = (uint32_t)((int64_t)z * plane4 + own);  // Philox group = word >> 2
         U4 o{0u, 0u, 0u, 0u};
         if (RULE == TIE_GLAUBER && (e0 | e1 | e2 | e3) != 0u) o = philox4x32_10_rk(gidx, t, (uint32_t)q, 0u, keys);
         uint4 nw;
@@ -311,7 +322,10 @@ __global__ void __launch_bounds__(256) k_sweep_zfast(uint32_t *lat, Geom g, int 
         nw.y = resolve<RULE>(s.y, g1, e1, o.y);
         nw.z = resolve<RULE>(s.z, g2, e2, o.z);
         nw.w = resolve<RULE>(s.w, g3, e3, o.w);
-        S4[(int64_t)z * plane4 + own] = nw;
+        *sp = nw;
+        sp += plane4;
+        gidx += gstep;
+        p ^= 1;
         cm = cc;
         cc = cp;
         sz = szp;
