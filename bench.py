@@ -604,9 +604,8 @@ def main():
     corr_tops = corr_ops / meas_avg_s / 1e12
     kname = {1: "k_sweep_word", 2: "k_sweep_zmarch", 3: "k_sweep_zfast", 4: "k_sweep_zdeep"}[tuned["variant"]]
     # DRAM bytes per launch from one ncu capture of the same kernel at L=2048 (sweep t=2);
-    # only quoted for the kernels those captures measured (k_sweep_zfast, 32-plane tiles;
-    # k_sweep_zdeep, 32-plane tiles, depth 3)
-    traffic = {3: 1.599e9, 4: 1.5967e9}.get(tuned["variant"]) if L == 2048 else None
+    # only quoted for the kernel that capture measured (k_sweep_zfast, 32-plane tiles)
+    traffic = {3: 1.596e9}.get(tuned["variant"]) if L == 2048 else None
     roof_sweep = {"kernel": kname + " (half-sweep)", "bound": "hbm", "achieved": sweep_gbs,
                   "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": sweep_gbs / pk["hbm_gbs"], "traffic": traffic,
                   "peak_src": pk["src"], "avg_launch_ms": sweep_avg_s * 1e3, "bytes_per_launch": bytes_per_launch,
