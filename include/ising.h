@@ -91,8 +91,8 @@ typedef struct {
  * matrix of the L positions over the L^2 lines of the axis, computed on the 5th-generation
  * tensor cores (tcgen05.mma, e4m3 operands loaded by TMA, fp32 accumulators in tensor memory;
  * exact: |G| <= L^2 <= 2^24); L a multiple of 128 in 256..2048; it allocates a scratch of
- * replicas * L^3/8 + L^3 bytes (the bit-transposed lattice and one axis expanded to e4m3:
- * 9.6 GB at L=2048) at its first use and keeps it (ising_release_scratch frees it).  AUTO:
+ * L^3 bytes (one axis of one replica expanded to e4m3: 8.6 GB at L=2048) at its first use and
+ * keeps it (ising_release_scratch frees it).  AUTO:
  * TENSOR for L >= 512 where it is supported and its scratch can be allocated (measured on
  * GB300: 1.9x faster than POPCOUNT at L=512, 3.5x at L=2048; slower at L=256), else POPCOUNT. */
 typedef enum { ISING_CORR_AUTO = 0, ISING_CORR_POPCOUNT = 1, ISING_CORR_TENSOR = 2 } ising_corr;

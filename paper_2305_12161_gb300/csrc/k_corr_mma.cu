@@ -16,6 +16,8 @@
 // distance; the records start from N/2.
 #include <cuda.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -28,35 +30,6 @@ constexpr int GT_KB = 128;       // K bytes (= lines) per stage and operand box
 constexpr int GT_STAGE_BYTES = (TM_T + GT_N) * GT_KB;
 constexpr int UMMA_WAIT_LIMIT = 1 << 22;  // try_wait rounds before a wait gives up
 
-// x-axis columns: bundle B = rows 32B .. 32B+31 (row = y + L z); XT[B*L + x] has bit i =
-// spin (x, row 32B + i) (1 = up).  One warp per (bundle, x-parity, word): 32 ballots.
-__global__ void k_transpose_x(const uint32_t *lat, Geom g, uint32_t *XT)
-{
-    const int r = blockIdx.y;
-    const uint32_t *S0 = lat + 2 * (int64_t)r * g.nw;
-    const uint32_t *S1 = S0 + g.nw;
-    const int L = g.L, W = g.W;
-    const int64_t nB = (int64_t)L * L / 32;
-    uint32_t *X = XT + (int64_t)r * nB * L;
-    const int lane = threadIdx.x & 31;
-    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t task = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); task < nB * 2 * W;
-         task += nwarps) {
-        const int64_t B = task / (2 * W);
-        const int rem = (int)(task - B * 2 * W);
-        const int pi = rem / W, kw = rem - pi * W;
-        const int64_t row = 32 * B + lane;
-        const int y = (int)(row % L), z = (int)(row / L);
-        const uint32_t v = (((pi + y + z) & 1) ? S1 : S0)[row * W + kw];
-        uint32_t mine = 0u;
-#pragma unroll 8
-        for (int k = 0; k < 32; ++k) {
-            const unsigned bal = __ballot_sync(0xffffffffu, (v >> k) & 1u);
-            if (lane == k) mine = bal;
-        }
-        X[B * L + 2 * (32 * kw + lane) + pi] = mine;
-    }
-}
 
 // Four e4m3 values from the four bits of n (n < 16): bit i -> byte i, +1.0 (0x38) when
 // set, -1.0 (0xB8) when clear.  The multiplier places bit i at bit 8i + 7 (and the other
@@ -105,45 +78,93 @@ __device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity)
 // contiguous KB (rows L^2 bytes apart would put every box's rows at a large power-of-two
 // stride).  Column cc of the panels (32 lines) is K = 32 cc .. 32 cc + 31.  Every word of the
 // lattice is expanded once instead of once per tile pair.
-__global__ void k_expand_e4m3(const uint32_t *S0, const uint32_t *S1, const uint32_t *XT, Geom g, int axis,
-                              uint8_t *E)
+__device__ __forceinline__ void store_e4m3_word(uint8_t *dst, uint32_t v)
 {
-    const int L = g.L, W = g.W;
-    const int64_t ncols = (int64_t)L * L / 32;
-    const int64_t total = ncols * L;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        int64_t cc;
-        int p;
-        uint32_t v;
-        if (axis == 0) {  // XT rows are contiguous in position: consecutive threads, consecutive p
-            cc = e / L;
-            p = (int)(e - cc * L);
-            v = __ldg(XT + cc * L + p);
-        } else {          // consecutive threads, consecutive columns: consecutive words of a row
-            p = (int)(e / ncols);
-            cc = e - (int64_t)p * ncols;
-            const int pi = (int)(cc / ((int64_t)L * W));
-            const int rem = (int)(cc - (int64_t)pi * L * W);
-            const int a = rem / W;
-            const int kw = rem - a * W;
-            const int y = axis == 1 ? p : a, z = axis == 1 ? a : p;
-            v = __ldg((((pi + y + z) & 1) ? S1 : S0) + ((int64_t)z * L + y) * W + kw);
+    uint4 lo, hi;
+    lo.x = e4m3x4(v & 0xFu);
+    lo.y = e4m3x4((v >> 4) & 0xFu);
+    lo.z = e4m3x4((v >> 8) & 0xFu);
+    lo.w = e4m3x4((v >> 12) & 0xFu);
+    hi.x = e4m3x4((v >> 16) & 0xFu);
+    hi.y = e4m3x4((v >> 20) & 0xFu);
+    hi.z = e4m3x4((v >> 24) & 0xFu);
+    hi.w = e4m3x4(v >> 28);
+    reinterpret_cast<uint4 *>(dst)[0] = lo;
+    reinterpret_cast<uint4 *>(dst)[1] = hi;
+}
+
+// x axis, straight from the packed store: a CTA stages both sublattices' words of 128
+// consecutive rows (row = y + L z; four bundles B of 32 rows) in shared memory with coalesced
+// loads; a warp then takes the words kw of sublattice-parity class pi of those rows (lane =
+// row in the bundle), transposes each 32 x 32 bit block in registers (five shuffle stages, each
+// swapping the off-diagonal half-blocks of size j between lanes r and r ^ j), after which lane
+// i holds, for site x = 2 (32 kw + i) + pi, the bits of the bundle's 32 rows; the four bundles
+// fill position x's 128-byte line of the chunk.
+__device__ __forceinline__ uint32_t transpose32_lane(uint32_t v, int lane)
+{
+    const uint32_t FULL = 0xffffffffu;
+    const uint32_t lows[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const int j = 16 >> k;
+        const uint32_t low = lows[k];
+        const uint32_t t = __shfl_xor_sync(FULL, v, j);
+        v = (lane & j) ? ((v & ~low) | ((t & ~low) >> j)) : ((v & low) | ((t & low) << j));
+    }
+    return v;
+}
+
+__global__ void __launch_bounds__(256) k_expand_x_e4m3(const uint32_t *S0, const uint32_t *S1, Geom g, uint8_t *E)
+{
+    extern __shared__ uint32_t xt[];  // [128 rows][2 W + 1]: both sublattices' words of a row
+    const int L = g.L, W = g.W, RS = 2 * W + 1;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t nB4 = (int64_t)L * L / 128;  // chunks of 128 rows = 4 bundles of 32
+    const int64_t blk = (int64_t)L * GT_KB;
+    for (int64_t B4 = blockIdx.x; B4 < nB4; B4 += gridDim.x) {
+        __syncthreads();  // the previous chunk's tile is consumed
+        // coalesced: consecutive threads read consecutive words of the chunk's rows
+        for (int e = tid; e < 128 * 2 * W; e += blockDim.x) {
+            const int ri = e / (2 * W), c = e - ri * 2 * W;
+            const int sub = c / W, kw = c - sub * W;
+            xt[ri * RS + c] = __ldg((sub ? S1 : S0) + (128 * B4 + ri) * W + kw);
         }
-        uint4 lo, hi;
-        lo.x = e4m3x4(v & 0xFu);
-        lo.y = e4m3x4((v >> 4) & 0xFu);
-        lo.z = e4m3x4((v >> 8) & 0xFu);
-        lo.w = e4m3x4((v >> 12) & 0xFu);
-        hi.x = e4m3x4((v >> 16) & 0xFu);
-        hi.y = e4m3x4((v >> 20) & 0xFu);
-        hi.z = e4m3x4((v >> 24) & 0xFu);
-        hi.w = e4m3x4(v >> 28);
-        uint4 *dst = reinterpret_cast<uint4 *>(E + (cc >> 2) * ((int64_t)L * GT_KB) + (int64_t)p * GT_KB + 32 * (cc & 3));
-        dst[0] = lo;
-        dst[1] = hi;
+        __syncthreads();
+        for (int task = warp; task < 2 * W; task += blockDim.x / 32) {
+            const int pi = task / W, kw = task - pi * W;
+            const int x = 2 * (32 * kw + lane) + pi;
+            uint8_t *dst = E + B4 * blk + (int64_t)x * GT_KB;  // one full 128-byte line per lane
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const int ri = 32 * b + lane;
+                const int64_t row = 128 * B4 + ri;
+                const int y = (int)(row % L), z = (int)(row / L);
+                const uint32_t v = xt[ri * RS + (((pi + y + z) & 1) ? W : 0) + kw];
+                store_e4m3_word(dst + 32 * b, transpose32_lane(v, lane));
+            }
+        }
     }
 }
 
+// y and z axes: blockIdx.y steps over positions p, the threads over the columns
+// cc = (pi L + a) W + kw of that position (consecutive words of one lattice row), so no 64-bit
+// division per word.
+__global__ void k_expand_e4m3(const uint32_t *S0, const uint32_t *S1, Geom g, int axis, uint8_t *E)
+{
+    const int L = g.L, W = g.W;
+    const int ncols = (int)((int64_t)L * L / 32);
+    const int64_t blk = (int64_t)L * GT_KB;  // bytes of one 128-line chunk of all positions
+    for (int p = blockIdx.y; p < L; p += gridDim.y) {
+        for (int cc = blockIdx.x * blockDim.x + threadIdx.x; cc < ncols; cc += gridDim.x * blockDim.x) {
+            const int kw = cc % W;
+            const int rest = cc / W;  // pi L + a
+            const int a = rest % L, pi = rest / L;
+            const int y = axis == 1 ? p : a, z = axis == 1 ? a : p;
+            const uint32_t v = __ldg((((pi + y + z) & 1) ? S1 : S0) + ((int64_t)z * L + y) * W + kw);
+            store_e4m3_word(E + (int64_t)(cc >> 2) * blk + (int64_t)p * GT_KB + 32 * (cc & 3), v);
+        }
+    }
+}
 
 __device__ __forceinline__ void mbar_expect_tx(uint32_t addr, uint32_t bytes)
 {
@@ -324,15 +345,15 @@ bool corr_mma_supported(int L) { return L >= 256 && L <= 2048 && L % TM_T == 0 &
 
 size_t corr_mma_scratch_bytes(int L, int R)
 {
-    return (size_t)R * (size_t)L * L * L / 8 + (size_t)L * L * L;  // transposed lattice + expanded axis
+    (void)R;  // replicas are multiplied one after the other through one expanded axis
+    return (size_t)L * L * L;
 }
 
 cudaError_t launch_corr_mma(const uint32_t *lat, int L, int R, int64_t *rec, uint32_t *scratch, int *err,
                             cudaStream_t s, int64_t *launches)
 {
     const Geom g = make_geom(L);
-    uint32_t *XT = scratch;
-    uint8_t *E = reinterpret_cast<uint8_t *>(scratch + (size_t)R * L * L * L / 32);
+    uint8_t *E = reinterpret_cast<uint8_t *>(scratch);
     EncodeTiledFn enc = encode_tiled();
     if (!enc) return cudaErrorNotSupported;
     // E viewed as rows of 128 bytes: row (chunk * L + position); boxes of 128 and 256 rows
@@ -348,12 +369,6 @@ cudaError_t launch_corr_mma(const uint32_t *lat, int L, int R, int64_t *rec, uin
             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
-    {
-        const int64_t tasks = (int64_t)L * L / 32 * 2 * g.W;
-        int64_t blocks = (tasks + 7) / 8;
-        if (blocks > 152 * 32) blocks = 152 * 32;
-        k_transpose_x<<<dim3((unsigned)blocks, (unsigned)R), 256, 0, s>>>(lat, g, XT);
-    }
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
@@ -367,12 +382,19 @@ cudaError_t launch_corr_mma(const uint32_t *lat, int L, int R, int64_t *rec, uin
     int split = sms / nunits;  // one CTA per SM: K slices x units <= SMs
     if (split < 1) split = 1;
     const int64_t H = L / 2, RL = 3 + 3 * (H + 1);
-    int64_t nl = 1;
+    const int ncols_e = (int)((int64_t)L * L / 32);
+    int64_t nl = 0;
     for (int r = 0; r < R; ++r) {
         const uint32_t *S0 = lat + 2 * (int64_t)r * g.nw;
         for (int axis = 0; axis < 3; ++axis) {
-            k_expand_e4m3<<<(unsigned)(sms * 8), 256, 0, s>>>(S0, S0 + g.nw, XT + (int64_t)r * L * L * L / 32, g,
-                                                             axis, E);
+            if (axis == 0) {  // 32 x 32 bit transposes, one warp per (bundle, parity, word)
+                const size_t xsm = (size_t)128 * (2 * g.W + 1) * sizeof(uint32_t);
+                k_expand_x_e4m3<<<(unsigned)std::min<int64_t>((int64_t)L * L / 128, (int64_t)sms * 4), 256, xsm, s>>>(
+                    S0, S0 + g.nw, g, E);
+            } else {          // positions over grid.y, columns over the threads
+                const dim3 eg((unsigned)std::max(1, std::min(8, ncols_e / 256)), (unsigned)L);
+                k_expand_e4m3<<<eg, 256, 0, s>>>(S0, S0 + g.nw, g, axis, E);
+            }
             k_gram_tma<<<(unsigned)(nunits * split), 128, smem, s>>>(tmA, tmB, L, nb, nunits, split,
                                                                      rec + r * RL + 3 + axis * (H + 1), err);
             nl += 2;
