@@ -184,6 +184,14 @@ typedef enum { ISING_FFT_SINGLE = 0, ISING_FFT_DOUBLE = 1 } ising_fft_precision;
 int64_t ising_radial_bins(int L);
 int ising_measure_radial(ising_ctx *ctx, int replica, int precision, double cval, double *C, double *S,
                          int64_t *count, double *ell, int64_t *inexact);
+/* Failure injection for tests: the next measurement that runs on the tensor cores loses one
+ * operand load in one CTA, so that CTA's bounded wait for it runs out after timeout_s
+ * (0 < timeout_s <= 60; it also becomes the bound of every later device-side wait of the
+ * context); the kernel gives up, releases its tensor memory and sets the context's error
+ * flag, and the synchronising call returns ISING_ETIMEOUT (the context is then poisoned).
+ * No fault is raised on the device. */
+int ising_inject_corr_stall(ising_ctx *ctx, double timeout_s);
+
 /* Free the scratch that measurements keep in the context (the radial measurement's transform
  * buffer and work area, the tensor-core correlation's transposed lattice); the next
  * measurement that needs it allocates it again.  Synchronises the context's stream. */

@@ -30,6 +30,8 @@ struct ising_ctx {
     uint32_t *xt = nullptr;      // tensor-core correlation: bit-transposed lattice (lazy)
     int *dev_err = nullptr;      // set by a device-side bounded wait that gave up
     int xt_refused = 0;          // the tensor-core scratch could not be allocated (AUTO falls back)
+    double wait_timeout_s = 2.0; // bound of each device-side wait (tensor-core path)
+    int inject_stall = 0;        // test hook: the next tensor-core measurement loses one load
     int64_t t = 0;
     int poisoned = 0;
     int64_t launches = 0;
@@ -408,6 +410,16 @@ int ising_release_scratch(ising_ctx *c)
     return ISING_OK;
 }
 
+int ising_inject_corr_stall(ising_ctx *c, double timeout_s)
+{
+    int s = check_ctx(c);
+    if (s) return s;
+    if (!(timeout_s > 0) || timeout_s > 60) return fail(c, ISING_EINVAL, "timeout must be in (0, 60] s");
+    c->wait_timeout_s = timeout_s;
+    c->inject_stall = 1;
+    return ISING_OK;
+}
+
 int ising_measure_ex(ising_ctx *c, int64_t *rec, double *derived, double cval, unsigned flags)
 {
     int s = check_ctx(c);
@@ -439,7 +451,10 @@ int ising_measure_ex(ising_ctx *c, int64_t *rec, double *derived, double cval, u
             method = CORR_POPCOUNT;
         }
     }
-    CK(c, launch_measure(c->lat, c->L, c->R, c->t, method, rdst, c->stream, &c->launches, c->xt, c->dev_err));
+    const int inject = method == CORR_TENSOR ? c->inject_stall : 0;
+    c->inject_stall = 0;
+    CK(c, launch_measure(c->lat, c->L, c->R, c->t, method, rdst, c->stream, &c->launches, c->xt, c->dev_err,
+                         c->wait_timeout_s, inject));
     double *ddst = nullptr;
     if (derived) {
         ddst = dev ? derived : c->der_dev;

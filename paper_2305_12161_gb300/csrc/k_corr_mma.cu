@@ -28,7 +28,7 @@ constexpr int GT_N = 256;        // B rows per CTA: two adjacent 128-position ti
 constexpr int GT_STAGES = 4;     // TMA pipeline depth (48 KB per stage)
 constexpr int GT_KB = 128;       // K bytes (= lines) per stage and operand box
 constexpr int GT_STAGE_BYTES = (TM_T + GT_N) * GT_KB;
-constexpr int UMMA_WAIT_LIMIT = 1 << 22;  // try_wait rounds before a wait gives up
+constexpr int UMMA_WAIT_LIMIT = 1 << 30;  // backstop on try_wait rounds (the wall-time bound comes first)
 
 
 // Four e4m3 values from the four bits of n (n < 16): bit i -> byte i, +1.0 (0x38) when
@@ -56,9 +56,18 @@ __device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr)
 constexpr uint32_t UMMA_IDESC = (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(GT_N >> 3) << 17) |
                                 ((uint32_t)(TM_T >> 4) << 24);
 
-// Bounded wait for phase `parity` of an mbarrier; false when it gave up.
-__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity)
+__device__ __forceinline__ uint64_t globaltimer_ns()
 {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for phase `parity` of an mbarrier for at most timeout_ns of wall time (and at most
+// UMMA_WAIT_LIMIT rounds); false when it gave up.
+__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity, uint64_t timeout_ns)
+{
+    const uint64_t t0 = globaltimer_ns();
     for (int it = 0; it < UMMA_WAIT_LIMIT; ++it) {
         uint32_t done;
         asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
@@ -66,6 +75,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity)
                      : "r"(addr), "r"(parity)
                      : "memory");
         if (done) return true;
+        if ((it & 255) == 255 && globaltimer_ns() - t0 > timeout_ns) return false;
     }
     return false;
 }
@@ -189,7 +199,8 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *tm,
 // its tensor memory.
 __global__ void __launch_bounds__(128, 1) k_gram_tma(const __grid_constant__ CUtensorMap tmA,
                                                      const __grid_constant__ CUtensorMap tmB, int L, int nb,
-                                                     int nunits, int split, int64_t *D, int *err)
+                                                     int nunits, int split, int64_t *D, int *err,
+                                                     uint64_t timeout_ns, int inject)
 {
     extern __shared__ __align__(1024) uint8_t gsm[];
     uint8_t *stage0 = gsm;  // [S][A 16 KB, B 32 KB]
@@ -239,13 +250,15 @@ __global__ void __launch_bounds__(128, 1) k_gram_tma(const __grid_constant__ CUt
     if (tid == 0) {  // producer
         for (int t = 0; t < n; ++t) {
             const int st = t % GT_STAGES;
-            if (t >= GT_STAGES && !mbar_wait(smem_u32(&empty[st]), (uint32_t)(((t / GT_STAGES) - 1) & 1))) {
+            if (t >= GT_STAGES &&
+                !mbar_wait(smem_u32(&empty[st]), (uint32_t)(((t / GT_STAGES) - 1) & 1), timeout_ns)) {
                 *flag = 0;
                 break;
             }
             if (!*(volatile int *)flag) break;
             const uint32_t sa = smem_u32(stage0 + st * GT_STAGE_BYTES);
             mbar_expect_tx(smem_u32(&full[st]), GT_STAGE_BYTES);
+            if (inject && blockIdx.x == 0 && t == 0) continue;  // test hook: this stage never fills
             tma_load_2d(sa, &tmA, 0, (c0 + t) * L + j0, smem_u32(&full[st]));
             tma_load_2d(sa + TM_T * GT_KB, &tmB, 0, (c0 + t) * L + s0, smem_u32(&full[st]));
         }
@@ -253,7 +266,7 @@ __global__ void __launch_bounds__(128, 1) k_gram_tma(const __grid_constant__ CUt
         int t = 0;
         for (; t < n; ++t) {
             const int st = t % GT_STAGES;
-            if (!mbar_wait(smem_u32(&full[st]), (uint32_t)((t / GT_STAGES) & 1))) {
+            if (!mbar_wait(smem_u32(&full[st]), (uint32_t)((t / GT_STAGES) & 1), timeout_ns)) {
                 *flag = 0;
                 break;
             }
@@ -273,7 +286,7 @@ __global__ void __launch_bounds__(128, 1) k_gram_tma(const __grid_constant__ CUt
         if (t > 0) {  // the last commit covers every MMA before it
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                 smem_u32(done)));
-            if (!mbar_wait(smem_u32(done), 0u)) *flag = 0;
+            if (!mbar_wait(smem_u32(done), 0u, timeout_ns)) *flag = 0;
         }
     }
     __syncthreads();
@@ -350,8 +363,9 @@ size_t corr_mma_scratch_bytes(int L, int R)
 }
 
 cudaError_t launch_corr_mma(const uint32_t *lat, int L, int R, int64_t *rec, uint32_t *scratch, int *err,
-                            cudaStream_t s, int64_t *launches)
+                            cudaStream_t s, int64_t *launches, double timeout_s, int inject)
 {
+    const uint64_t timeout_ns = (uint64_t)(timeout_s * 1e9);
     const Geom g = make_geom(L);
     uint8_t *E = reinterpret_cast<uint8_t *>(scratch);
     EncodeTiledFn enc = encode_tiled();
@@ -396,7 +410,8 @@ cudaError_t launch_corr_mma(const uint32_t *lat, int L, int R, int64_t *rec, uin
                 k_expand_e4m3<<<eg, 256, 0, s>>>(S0, S0 + g.nw, g, axis, E);
             }
             k_gram_tma<<<(unsigned)(nunits * split), 128, smem, s>>>(tmA, tmB, L, nb, nunits, split,
-                                                                     rec + r * RL + 3 + axis * (H + 1), err);
+                                                                     rec + r * RL + 3 + axis * (H + 1), err,
+                                                                     timeout_ns, inject && r == 0 && axis == 1);
             nl += 2;
         }
     }

@@ -338,7 +338,8 @@ static cudaError_t launch_corr(const uint32_t *lat, const Geom &g, int R, int64_
 }
 
 cudaError_t launch_measure(const uint32_t *lat, int L, int R, int64_t t, int corr, int64_t *rec, cudaStream_t s,
-                           int64_t *launches, uint32_t *xt_scratch, int *err)
+                           int64_t *launches, uint32_t *xt_scratch, int *err, double wait_timeout_s,
+                           int inject_stall)
 {
     const Geom g = make_geom(L);
     const int64_t RL = 3 + 3 * (int64_t)(L / 2 + 1);
@@ -351,7 +352,7 @@ cudaError_t launch_measure(const uint32_t *lat, int L, int R, int64_t t, int cor
     int n = 2;
     if (corr == CORR_TENSOR) {
         if (!xt_scratch || !err || !corr_mma_supported(L)) return cudaErrorInvalidValue;
-        const cudaError_t e = launch_corr_mma(lat, L, R, rec, xt_scratch, err, s, nullptr);
+        const cudaError_t e = launch_corr_mma(lat, L, R, rec, xt_scratch, err, s, nullptr, wait_timeout_s, inject_stall);
         if (e != cudaSuccess) return e;
         n += 2;
     } else if (corr) {

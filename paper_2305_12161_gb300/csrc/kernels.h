@@ -96,12 +96,15 @@ cudaError_t launch_unpack(const uint32_t *lat, int8_t *plain, int L, int R, cuda
 // and err (a device int set to 1 if a bounded wait of the tensor-core kernel gave up; the
 // records are then incomplete).
 enum CorrMethod : int { CORR_NONE = 0, CORR_POPCOUNT = 1, CORR_TENSOR = 2 };
+// wait_timeout_s bounds each device-side wait of the tensor-core path (wall time);
+// inject_stall (tests) makes one of its CTAs skip a load so that a wait runs out.
 cudaError_t launch_measure(const uint32_t *lat, int L, int R, int64_t t, int corr, int64_t *rec,
-                           cudaStream_t s, int64_t *launches, uint32_t *xt_scratch = nullptr, int *err = nullptr);
+                           cudaStream_t s, int64_t *launches, uint32_t *xt_scratch = nullptr, int *err = nullptr,
+                           double wait_timeout_s = 2.0, int inject_stall = 0);
 bool corr_mma_supported(int L);
 size_t corr_mma_scratch_bytes(int L, int R);
 cudaError_t launch_corr_mma(const uint32_t *lat, int L, int R, int64_t *rec, uint32_t *xt_scratch, int *err,
-                            cudaStream_t s, int64_t *launches);
+                            cudaStream_t s, int64_t *launches, double timeout_s, int inject);
 // derived: R x [e, m, l_E, l_C]
 cudaError_t launch_derived(const int64_t *rec, int L, int R, double c, bool connected, double *derived,
                            cudaStream_t s, int64_t *launches);

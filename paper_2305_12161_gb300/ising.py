@@ -76,6 +76,7 @@ def lib() -> ctypes.CDLL:
                 "ising_measure_ex": (ctypes.c_int, [vp, vp, vp, ctypes.c_double, ctypes.c_uint]),
                 "ising_radial_bins": (ctypes.c_int64, [ctypes.c_int]),
                 "ising_release_scratch": (ctypes.c_int, [vp]),
+                "ising_inject_corr_stall": (ctypes.c_int, [vp, ctypes.c_double]),
                 "ising_measure_radial": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, vp, vp,
                                                         vp, vp, vp]),
                 "ising_get_spins": (ctypes.c_int, [vp, ctypes.c_int, vp]),
@@ -248,6 +249,10 @@ class Ising:
                                                n.ctypes.data, ctypes.addressof(ell), ctypes.addressof(bad)),
                     "ising_measure_radial")
         return {"C": C, "S": S, "count": n, "ell": ell.value, "inexact": bad.value}
+
+    def inject_corr_stall(self, timeout_s: float = 0.5) -> None:
+        """Test hook: the next tensor-core measurement's bounded wait runs out (ISING_ETIMEOUT)."""
+        self._check(lib().ising_inject_corr_stall(self._h, timeout_s), "ising_inject_corr_stall")
 
     def release_scratch(self) -> None:
         """Free the measurement scratch kept in the context (radial FFT buffer, etc.)."""

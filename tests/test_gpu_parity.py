@@ -246,3 +246,23 @@ def test_tensor_core_correlation_closed_forms(ising):
 def test_tensor_core_correlation_rejects_unsupported_sizes(ising):
     with pytest.raises(ising.IsingError):
         ising.Ising(64, replicas=1, seed=1, corr=ising.CORR_TENSOR)
+
+
+def test_tensor_core_wait_times_out_instead_of_hanging(ising):
+    import time
+    with ising.Ising(512, replicas=1, seed=2, corr=ising.CORR_TENSOR) as q:
+        q.sweep(2)
+        good = q.measure()
+        q.inject_corr_stall(0.3)
+        t0 = time.time()
+        with pytest.raises(ising.IsingError) as e:
+            q.measure()
+        assert e.value.status == ising.ISING_ETIMEOUT
+        assert time.time() - t0 < 30
+        with pytest.raises(ising.IsingError) as e:
+            q.sweep(1)
+        assert e.value.status == ising.ISING_EPOISONED
+    # the device is still usable, and the same measurement is exact again in a new context
+    with ising.Ising(512, replicas=1, seed=2, corr=ising.CORR_TENSOR) as q:
+        q.sweep(2)
+        assert np.array_equal(q.measure(), good)
