@@ -584,7 +584,11 @@ def main():
     leg_launches = [sum(n for _, _, n, lg in sweep_events if lg == g) for g in (0, 1)]
     meas_ms = sum(a.elapsed_time(b) for a, b in meas_events)
     pk = _peaks()
-    bytes_per_launch = 3 * (N // 2) / 8  # read q, read q-bar, write q: 1 bit each per site
+    fused = tuned["variant"] == 5
+    # a half-sweep reads q and q-bar and writes q (1 bit per site each: 3 N/16 bytes); the fused
+    # sweep reads both sublattices and writes both (N/4 bytes) and updates all N sites
+    bytes_per_launch = N / 4 if fused else 3 * (N // 2) / 8
+    sites_per_launch = N if fused else N // 2
     sweep_avg_s = sweep_ms * 1e-3 / sweep_launches
     sweep_gbs = bytes_per_launch / sweep_avg_s / 1e9
     # correlation pass: XOR+popc word operations, 3 axes x L/2 lags x N/32 words
@@ -602,14 +606,16 @@ def main():
     words_per_clk = 16 / (f_pop * p_pop + (1 - f_pop) * p_csa)
     popc_peak = 152 * words_per_clk * pk["sm_max_mhz"] * 1e6 / 1e12  # T word pairs/s
     corr_tops = corr_ops / meas_avg_s / 1e12
-    kname = {1: "k_sweep_word", 2: "k_sweep_zmarch", 3: "k_sweep_zfast", 4: "k_sweep_zdeep"}[tuned["variant"]]
+    kname = {1: "k_sweep_word", 2: "k_sweep_zmarch", 3: "k_sweep_zfast", 4: "k_sweep_zdeep",
+             5: "k_mcs_fused"}[tuned["variant"]]
     # DRAM bytes per launch from one ncu capture of the same kernel at L=2048 (sweep t=2);
     # only quoted for the kernel that capture measured (k_sweep_zfast, 32-plane tiles)
     traffic = {3: 1.596e9}.get(tuned["variant"]) if L == 2048 else None
-    roof_sweep = {"kernel": kname + " (half-sweep)", "bound": "hbm", "achieved": sweep_gbs,
+    roof_sweep = {"kernel": kname + (" (whole sweep)" if fused else " (half-sweep)"), "bound": "hbm",
+                  "achieved": sweep_gbs,
                   "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": sweep_gbs / pk["hbm_gbs"], "traffic": traffic,
                   "peak_src": pk["src"], "avg_launch_ms": sweep_avg_s * 1e3, "bytes_per_launch": bytes_per_launch,
-                  "updates_per_ns": (N // 2) / sweep_avg_s / 1e9}
+                  "updates_per_ns": sites_per_launch / sweep_avg_s / 1e9}
     if tensor_corr:
         # tensor-core path: the upper block triangle of the three axes' Gram matrices,
         # npairs tiles of 128 x 128 over K = L^2 lines, 2 flops per multiply-add; against the
@@ -647,9 +653,9 @@ def main():
             "breakdown_ms_per_step": {"sweeps": sweep_ms / args.steps, "measurements": meas_ms / args.steps,
                                       "sweeps_leg_i_t0": leg_ms[0] / args.steps,
                                       "sweeps_leg_ii_t1e4": leg_ms[1] / args.steps},
-            "sweep_updates_per_ns_by_leg": [(N // 2) * n / (ms_ * 1e-3) / 1e9 if ms_ > 0 else None
+            "sweep_updates_per_ns_by_leg": [sites_per_launch * n / (ms_ * 1e-3) / 1e9 if ms_ > 0 else None
                                             for n, ms_ in zip(leg_launches, leg_ms)],
-            "sweep_only_updates_per_ns": world * (N // 2) / sweep_avg_s / 1e9,
+            "sweep_only_updates_per_ns": world * sites_per_launch / sweep_avg_s / 1e9,
             "sweep_config": tuned,
             "corr_method": "tensor cores (tcgen05 Gram)" if tensor_corr else "bit counts",
             "clocks": clk, "e2e": e2e, "gpu_launches": launches, "batched": batched,

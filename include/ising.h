@@ -73,11 +73,15 @@ typedef struct {
     int variant;    /* packed sweep kernel variant, 0 = automatic (see ising_variants):
                        1 one thread per word (any L), 2 z-marching tiles (L multiple of 256),
                        3 z-marching specialised on the row width (L = 256, 512, 1024, 2048),
-                       4 as 3 with a deeper copy pipeline and fewer registers */
+                       4 as 3 with a deeper copy pipeline and fewer registers,
+                       5 one launch per sweep updating both sublattices (L = 256 .. 2048, powers
+                         of two; holds a second packed store of the same size, the two swap
+                         roles every sweep) */
     int tile_y;     /* packed z-marching variant: rows per tile (0 = automatic); variant 3
                        (z-marching specialised on the row width) fixes it to 256/(L/256) */
-    int tile_z;     /* packed z-marching variant: planes per tile (0 = automatic) */
-    int depth;      /* variant 4: planes in flight in the copy pipeline, 2..4 (0 = 3) */
+    int tile_z;     /* packed z-marching variants: planes per tile (0 = automatic) */
+    int depth;      /* variant 4: planes in flight in the copy pipeline, 2..4 (0 = 3);
+                       variant 5: copy groups in flight, 2 or 3 (0 = 2) */
     int cycle;      /* ising_cycle: sublattice order of each sweep */
     int corr;       /* ising_corr: how the correlation sums D_a(r) are computed */
     int scheme;     /* ising_scheme: checkerboard or double checkerboard */

@@ -24,6 +24,7 @@ struct ising_ctx {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     uint32_t *lat = nullptr;     // packed store (PACKED form), or measurement copy (PLAIN form)
+    uint32_t *lat_alt = nullptr; // second packed store of the fused sweep (VARIANT_ZFUSE)
     int8_t *plain = nullptr;     // PLAIN form lattice
     int64_t *rec_dev = nullptr;  // R records
     double *der_dev = nullptr;   // R x 4
@@ -147,10 +148,10 @@ int64_t ising_launch_count(const ising_ctx *c) { return c ? c->launches : -1; }
 
 int ising_variants(int *ids, int cap)
 {
-    const int all[4] = {VARIANT_WORD, VARIANT_ZMARCH, VARIANT_ZFAST, VARIANT_ZDEEP};
-    if (!ids) return 4;
+    const int all[5] = {VARIANT_WORD, VARIANT_ZMARCH, VARIANT_ZFAST, VARIANT_ZDEEP, VARIANT_ZFUSE};
+    if (!ids) return 5;
     int n = 0;
-    for (int i = 0; i < 4 && n < cap; ++i) ids[n++] = all[i];
+    for (int i = 0; i < 5 && n < cap; ++i) ids[n++] = all[i];
     return n;
 }
 
@@ -162,6 +163,7 @@ int ising_destroy(ising_ctx *c)
         // stream-ordered frees: releasing a context does not synchronise other streams
         if (c->stream) {
             if (c->lat) cudaFreeAsync(c->lat, c->stream);
+            if (c->lat_alt) cudaFreeAsync(c->lat_alt, c->stream);
             if (c->plain) cudaFreeAsync(c->plain, c->stream);
             if (c->rec_dev) cudaFreeAsync(c->rec_dev, c->stream);
             if (c->der_dev) cudaFreeAsync(c->der_dev, c->stream);
@@ -226,8 +228,10 @@ int ising_create_ex(ising_ctx **out, int L, int R, uint64_t seed, const ising_op
     if (o.variant == 0) {
         c->cfg = default_sweep_config(L, R);
     } else {
-        c->cfg = SweepConfig{o.variant, o.tile_y, o.tile_z, o.depth ? o.depth : 3};
-        if ((c->cfg.variant == VARIANT_ZMARCH || c->cfg.variant == VARIANT_ZFAST || c->cfg.variant == VARIANT_ZDEEP) &&
+        c->cfg = SweepConfig{o.variant, o.tile_y, o.tile_z,
+                             o.variant == VARIANT_ZFUSE ? o.depth : (o.depth ? o.depth : 3)};
+        if ((c->cfg.variant == VARIANT_ZMARCH || c->cfg.variant == VARIANT_ZFAST || c->cfg.variant == VARIANT_ZDEEP ||
+             c->cfg.variant == VARIANT_ZFUSE) &&
             (o.tile_y == 0 || o.tile_z == 0)) {
             if (L >= 256 && L % 256 == 0) {
                 const int W4 = L / 256;
@@ -235,13 +239,17 @@ int ising_create_ex(ising_ctx **out, int L, int R, uint64_t seed, const ising_op
                 if (!c->cfg.tile_z) c->cfg.tile_z = std::min(L, 16);
             }
         }
-        if ((c->cfg.variant == VARIANT_ZFAST || c->cfg.variant == VARIANT_ZDEEP) && L >= 256 && L % 256 == 0)
+        if ((c->cfg.variant == VARIANT_ZFAST || c->cfg.variant == VARIANT_ZDEEP || c->cfg.variant == VARIANT_ZFUSE) &&
+            L >= 256 && L % 256 == 0)
             c->cfg.tile_y = 256 / (L / 256);
         if (!sweep_config_valid(L, c->cfg)) return bail(ISING_EINVAL);
     }
     // stream-ordered allocations (no implicit device synchronisation)
     const size_t pbytes = lattice_bytes_packed(L, R);
     if (cudaMallocAsync((void **)&c->lat, pbytes, c->stream) != cudaSuccess) return bail(ISING_ENOMEM);
+    if (c->cfg.variant == VARIANT_ZFUSE && o.form == ISING_FORM_PACKED && o.scheme == ISING_SCHEME_CHECKERBOARD &&
+        cudaMallocAsync((void **)&c->lat_alt, pbytes, c->stream) != cudaSuccess)
+        return bail(ISING_ENOMEM);
     if (o.form == ISING_FORM_PLAIN) {
         const size_t nbytes = (size_t)R * (size_t)L * L * L;
         if (cudaMallocAsync((void **)&c->plain, nbytes, c->stream) != cudaSuccess) return bail(ISING_ENOMEM);
@@ -320,6 +328,9 @@ int ising_sweep(ising_ctx *c, int64_t n)
     else if (c->opts.form == ISING_FORM_PLAIN)
         e = launch_sweeps_plain(c->plain, c->L, c->R, c->seed, c->opts.tie, c->t, n, c->opts.cycle, c->stream,
                                 &c->launches);
+    else if (c->cfg.variant == VARIANT_ZFUSE)
+        e = launch_sweeps_fused(&c->lat, &c->lat_alt, c->L, c->R, c->seed, c->opts.tie, c->t, n, c->opts.cycle,
+                                c->cfg.tile_z, c->cfg.depth, c->stream, &c->launches);
     else
         e = launch_sweeps_packed(c->lat, c->L, c->R, c->seed, c->opts.tie, c->t, n, c->opts.cycle, c->cfg, c->stream,
                                  &c->launches);
@@ -618,6 +629,11 @@ int ising_tune_sweep(int L, int replicas, int probe_mcs, const ising_opts *base,
                 if (sweep_config_valid(L, cd)) cands.push_back(cd);
             }
         }
+        for (int tz : {16, 32, 64, 128})
+            for (int mb : {2, 3}) {
+                const SweepConfig cf{VARIANT_ZFUSE, 256 / W4, tz, mb};
+                if (sweep_config_valid(L, cf)) cands.push_back(cf);
+            }
     }
     double best_ms = 1e300;
     bool found = false;

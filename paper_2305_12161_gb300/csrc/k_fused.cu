@@ -1,0 +1,321 @@
+// One whole Monte Carlo sweep (both half-sweeps, Methods "Checkerboard update") in one pass
+// over the lattice: temporal blocking of the red-black order.  The pass reads the store of
+// sweep t (`cur`) and writes the store of sweep t+1 (`nxt`), so no CTA ever reads a value
+// that another CTA of the same launch has already replaced.
+//
+// A CTA owns TY full rows and TZ planes and marches along z.  With A the sublattice updated
+// first and B the other, step k updates A on plane zA = z0 - 1 + k for the tile's rows and
+// one halo row on each side, then B on plane zB = zA - 1 for the tile's rows; B's neighbours
+// are A's new values of planes zB - 1 .. zB + 1, which this CTA has just computed, halo
+// rows included.  A on the halo planes z0 - 1 and z0 + TZ and on the halo rows is computed
+// but not stored: the CTA that owns them stores the same values.  Every update is the
+// half-sweep's: same rule, same Philox bits (phase = the sublattice, counter word = the
+// storage group), so the trajectory is bit-identical to two half-sweep launches.
+//
+// Per sweep the store is read once (plus L2-served halo rows and planes) and written once:
+// N/4 bytes, against 3 N/8 for two half-sweeps.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace ising {
+
+namespace {
+
+__device__ __forceinline__ void fcp16(void *smem, const void *gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void fcommit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void fwait()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// x-neighbour words of the 128 sites of uint4 C: the same-k neighbour is C itself, the other
+// is C shifted by one bit with the edge bit of the adjacent uint4 (direction by p).
+__device__ __forceinline__ uint4 xshift(const uint4 &C, uint32_t edge_left_w, uint32_t edge_right_x, int p)
+{
+    uint4 X;
+    if (p == 0) {
+        X.x = __funnelshift_l(edge_left_w, C.x, 1);
+        X.y = __funnelshift_l(C.x, C.y, 1);
+        X.z = __funnelshift_l(C.y, C.z, 1);
+        X.w = __funnelshift_l(C.z, C.w, 1);
+    } else {
+        X.x = __funnelshift_r(C.x, C.y, 1);
+        X.y = __funnelshift_r(C.y, C.z, 1);
+        X.z = __funnelshift_r(C.z, C.w, 1);
+        X.w = __funnelshift_r(C.w, edge_right_x, 1);
+    }
+    return X;
+}
+
+__device__ __forceinline__ uint32_t maj3(uint32_t a, uint32_t b, uint32_t c) { return (a & b) | (c & (a ^ b)); }
+
+// New spins of the 128 sites of one uint4 (T -> 0 Glauber, Eq. 6).  With u the number of up
+// neighbours and tau the tie bit (the old spin for the rule that never flips at zero energy,
+// its complement for the rule that always flips, the old spin xor the random bit for Glauber),
+// the new spin is [u + tau >= 4]: up where u >= 4, tau where u = 3, down where u <= 2.  Two
+// full adders give u = s1 + s2 + 2 (c1 + c2); a third adds s1 + s2 + tau = s3 + 2 c3, so the
+// new spin is the majority of c1, c2, c3.  Glauber draws Philox only where some site of the
+// group has u = 3, i.e. s1 != s2 and c1 != c2.
+template <int RULE>
+__device__ __forceinline__ uint4 update4(const uint4 &s, const uint4 &C, const uint4 &X, const uint4 &ym,
+                                         const uint4 &yp, const uint4 &zm, const uint4 &zp, uint32_t group,
+                                         uint32_t t, uint32_t q, const PhiloxKeys &keys)
+{
+    const uint32_t s1x = C.x ^ X.x ^ ym.x, c1x = maj3(C.x, X.x, ym.x);
+    const uint32_t s1y = C.y ^ X.y ^ ym.y, c1y = maj3(C.y, X.y, ym.y);
+    const uint32_t s1z = C.z ^ X.z ^ ym.z, c1z = maj3(C.z, X.z, ym.z);
+    const uint32_t s1w = C.w ^ X.w ^ ym.w, c1w = maj3(C.w, X.w, ym.w);
+    const uint32_t s2x = yp.x ^ zm.x ^ zp.x, c2x = maj3(yp.x, zm.x, zp.x);
+    const uint32_t s2y = yp.y ^ zm.y ^ zp.y, c2y = maj3(yp.y, zm.y, zp.y);
+    const uint32_t s2z = yp.z ^ zm.z ^ zp.z, c2z = maj3(yp.z, zm.z, zp.z);
+    const uint32_t s2w = yp.w ^ zm.w ^ zp.w, c2w = maj3(yp.w, zm.w, zp.w);
+    uint4 tau;
+    if (RULE == TIE_GLAUBER) {
+        const uint32_t tie = ((s1x ^ s2x) & (c1x ^ c2x)) | ((s1y ^ s2y) & (c1y ^ c2y)) |
+                             ((s1z ^ s2z) & (c1z ^ c2z)) | ((s1w ^ s2w) & (c1w ^ c2w));
+        U4 o{0u, 0u, 0u, 0u};
+        if (tie != 0u) o = philox4x32_10_rk(group, t, q, 0u, keys);
+        tau = make_uint4(s.x ^ o.x, s.y ^ o.y, s.z ^ o.z, s.w ^ o.w);
+    } else if (RULE == TIE_ALWAYS) {
+        tau = make_uint4(~s.x, ~s.y, ~s.z, ~s.w);
+    } else {
+        tau = s;
+    }
+    return make_uint4(maj3(c1x, c2x, maj3(s1x, s2x, tau.x)), maj3(c1y, c2y, maj3(s1y, s2y, tau.y)),
+                      maj3(c1z, c2z, maj3(s1z, s2z, tau.z)), maj3(c1w, c2w, maj3(s1w, s2w, tau.w)));
+}
+
+}  // namespace
+
+// Shared memory: NS copy slots, each one B plane (rows y0-2 .. y0+TY+1) and one old-A plane
+// (rows y0-1 .. y0+TY); two slots of new A (rows y0-1 .. y0+TY).
+template <int W4, int NS>
+static constexpr size_t fused_smem_bytes()
+{
+    constexpr int TY = 256 / W4;
+    return sizeof(uint4) * (size_t)(NS * (2 * TY + 6) * W4 + 2 * (TY + 2) * W4);
+}
+
+// Thread tid owns column cx = lane % W4 of row y0 + ty (the rows of a warp share their parity,
+// as in the half-sweep kernel) for both sublattices, so the B update finds its own column's
+// new A on planes zB - 1, zB, zB + 1 in registers and reads only rows y +- 1 from shared memory.
+// x-edge words come from the neighbouring lane of the row by a shuffle.  Lanes 0 .. 2 W4 - 1
+// of warp 0 also update A on the halo rows.  Copy group g brings B plane z0 - 2 + g and, for
+// g >= 2, old-A plane z0 - 1 + (g - 2); step k reads the slots of groups k .. k + 2 and
+// refills the slot of group k - 1 with group k + NS - 1, so NS - 3 groups stay in flight.
+// Offsets into a sublattice are 32-bit uint4 indices (L^3 / 256 < 2^31).
+template <int RULE, int W4, int NS>
+__global__ void __launch_bounds__(256, 3) k_mcs_fused(const uint32_t *__restrict__ cur, uint32_t *__restrict__ nxt,
+                                                      Geom g, int mixed, uint32_t t, uint64_t seed, int TZ)
+{
+    constexpr int NT = 256, TY = NT / W4, RW = 32 / W4;
+    constexpr int RB = TY + 4;                 // B rows of a slot
+    constexpr int RA = TY + 2;                 // A rows of a slot, and of a new-A slot
+    constexpr int NB = RB * W4;                // B items of a slot (A items follow)
+    constexpr int SLOT = (RB + RA) * W4;
+    constexpr int NCP = (SLOT + NT - 1) / NT;  // copies per thread per group
+    constexpr uint32_t FULL = 0xffffffffu;
+    constexpr uint32_t HMASK = 2 * W4 >= 32 ? FULL : ((1u << (2 * W4)) - 1u);
+    extern __shared__ uint4 fsm[];
+    uint4 *ring = fsm;              // [NS][SLOT], group g in slot g % NS
+    uint4 *anew = fsm + NS * SLOT;  // [2][RA * W4]
+    const int L = g.L;
+    const int tid = threadIdx.x;
+    const int nty = L / TY;
+    const int y0 = (int)(blockIdx.x % nty) * TY;
+    const int z0 = (int)(blockIdx.x / nty) * TZ;
+    const int r = blockIdx.y;
+    const uint64_t S = seed + (uint64_t)r;
+    // sublattice updated first: 0 (01 cycle) or the sweep's drawn order (mixed cycle)
+    int A = 0;
+    if (mixed) A = (int)(philox4x32_10(0u, t, 5u, 0u, (uint32_t)S, (uint32_t)(S >> 32)).x & 1u);
+    const int B = 1 - A;
+    const int32_t plane4 = L * W4;
+    const int32_t vol4 = L * plane4;
+    const uint4 *Acur = reinterpret_cast<const uint4 *>(cur + (2 * (int64_t)r + A) * g.nw);
+    const uint4 *Bcur = reinterpret_cast<const uint4 *>(cur + (2 * (int64_t)r + B) * g.nw);
+    uint4 *Anxt = reinterpret_cast<uint4 *>(nxt + (2 * (int64_t)r + A) * g.nw);
+    uint4 *Bnxt = reinterpret_cast<uint4 *>(nxt + (2 * (int64_t)r + B) * g.nw);
+    const PhiloxKeys keys = philox_keys(S);
+    auto wrapL = [&](int a) { return a < 0 ? a + L : (a >= L ? a - L : a); };
+
+    // copies: slot item e = tid + j NT; its offset within a plane is fixed over the march
+    int32_t coff[NCP];
+#pragma unroll
+    for (int j = 0; j < NCP; ++j) {
+        const int e = tid + j * NT;
+        const int ea = e < NB ? e : e - NB;
+        coff[j] = wrapL(y0 + ea / W4 - (e < NB ? 2 : 1)) * W4 + (ea & (W4 - 1));
+    }
+    int32_t ob = wrapL(z0 - 2) * plane4;  // B plane of the next group
+    int32_t oa = wrapL(z0 - 1) * plane4;  // A plane of the next group that has one
+    auto issue = [&](int gi, int slot) {
+        uint4 *dst = ring + slot * SLOT;
+        if (gi <= TZ + 3) {
+            const bool wa = gi >= 2;
+#pragma unroll
+            for (int j = 0; j < NCP; ++j) {
+                const int e = tid + j * NT;
+                if (e < NB)
+                    fcp16(dst + e, Bcur + (ob + coff[j]));
+                else if (e < SLOT && wa)
+                    fcp16(dst + e, Acur + (oa + coff[j]));
+            }
+            ob += plane4;
+            if (ob == vol4) ob = 0;
+            if (wa) {
+                oa += plane4;
+                if (oa == vol4) oa = 0;
+            }
+        }
+        fcommit();
+    };
+
+    const int warp = tid >> 5, lane = tid & 31;
+    const int cx = lane & (W4 - 1);
+    const int ty = (warp >> 1) * 2 * RW + (warp & 1) + 2 * (lane / W4);
+    const int32_t own = (y0 + ty) * W4 + cx;
+    const int rB = (ty + 2) * W4 + cx;  // own row in a B slot
+    const int rN = (ty + 1) * W4 + cx;  // own row in an A slot
+    const int srcl = (cx + W4 - 1) & (W4 - 1), srcr = (cx + 1) & (W4 - 1);
+    // halo lanes: row hr (0: y0-1, 1: y0+TY)
+    const bool hl = warp == 0 && lane < 2 * W4;
+    const int hr = lane / W4;
+    const int hB = (hr ? TY + 2 : 1) * W4 + cx;  // halo row in a B slot
+    const int hN = (hr ? TY + 1 : 0) * W4 + cx;  // halo row in an A slot
+    const int32_t dh = wrapL(hr ? y0 + TY : y0 - 1) * W4 + cx - own;
+
+#pragma unroll 1
+    for (int gi = 0; gi < NS - 1; ++gi) issue(gi, gi);
+    int32_t oA = wrapL(z0 - 1) * plane4 + own;  // plane zA, own column
+    int32_t oB = 0;                             // plane zA - 1 (= zB), own column
+    int p = (ty + z0 - 1 + A) & 1;              // x direction on plane zA (y0 even); also B's on zA - 1
+    fwait<NS - 3>();  // groups 0 and 1
+    __syncthreads();
+    uint4 bm = ring[0 * SLOT + rB];  // B plane zA - 1, own column
+    uint4 bc = ring[1 * SLOT + rB];  // B plane zA
+    uint4 a1 = make_uint4(0u, 0u, 0u, 0u), a2 = a1;  // new A, planes zA - 1 and zA - 2, own column
+    int sl0 = 0;  // slot of group k
+#pragma unroll 1
+    for (int k = 0; k <= TZ + 1; ++k) {
+        fwait<NS - 4>();  // group k + 2 has landed
+        __syncthreads();
+        const int sl1 = sl0 == NS - 1 ? 0 : sl0 + 1, sl2 = sl1 == NS - 1 ? 0 : sl1 + 1;
+        issue(k + NS - 1, sl0 == 0 ? NS - 1 : sl0 - 1);  // the slot of group k - 1, last read in step k - 1
+        const uint4 *Bsm = ring + sl0 * SLOT;  // B plane zA - 1
+        const uint4 *Bs0 = ring + sl1 * SLOT;  // B plane zA
+        const uint4 *Bsp = ring + sl2 * SLOT;  // B plane zA + 1, old A plane zA (at NB)
+        sl0 = sl1;
+        uint4 *An = anew + (k & 1) * RA * W4;
+        // A, own column
+        const uint4 bp = Bsp[rB];
+        uint4 a0;
+        {
+            const uint32_t e = __shfl_sync(FULL, p ? bc.x : bc.w, p ? srcr : srcl, W4);
+            const uint4 X = xshift(bc, e, e, p);
+            a0 = update4<RULE>(Bsp[NB + rN], bc, X, Bs0[rB - W4], Bs0[rB + W4], bm, bp, (uint32_t)oA, t,
+                               (uint32_t)A, keys);
+            An[rN] = a0;
+            if (k >= 1 && k <= TZ) Anxt[oA] = a0;
+        }
+        // A, halo rows: row y0 - 1 is odd (the other direction than warp 0's even rows), row
+        // y0 + TY even (the same)
+        if (hl) {
+            const uint4 hbc = Bs0[hB];
+            const int ph = p ^ 1 ^ hr;
+            const uint32_t e = __shfl_sync(HMASK, ph ? hbc.x : hbc.w, ph ? srcr : srcl, W4);
+            const uint4 X = xshift(hbc, e, e, ph);
+            An[hN] = update4<RULE>(Bsp[NB + hN], hbc, X, Bs0[hB - W4], Bs0[hB + W4], Bsm[hB], Bsp[hB],
+                                   (uint32_t)(oA + dh), t, (uint32_t)A, keys);
+        }
+        // B on plane zB = zA - 1, own column: new A of planes zB - 1, zB, zB + 1 are a2, a1, a0
+        if (k >= 2) {
+            const uint4 *Ap = anew + ((k - 1) & 1) * RA * W4;  // new A, plane zB
+            const uint32_t e = __shfl_sync(FULL, p ? a1.x : a1.w, p ? srcr : srcl, W4);
+            const uint4 X = xshift(a1, e, e, p);
+            Bnxt[oB] = update4<RULE>(bm, a1, X, Ap[rN - W4], Ap[rN + W4], a2, a0, (uint32_t)oB, t, (uint32_t)B, keys);
+        }
+        a2 = a1;
+        a1 = a0;
+        bm = bc;
+        bc = bp;
+        oB = oA;
+        oA += plane4;
+        if (oA >= vol4) oA -= vol4;
+        p ^= 1;
+    }
+    fwait<0>();
+}
+
+bool fused_config_valid(int L, int TZ, int depth)
+{
+    return L >= 256 && L <= 2048 && L % 256 == 0 && (L & (L - 1)) == 0 && TZ >= 1 && L % TZ == 0 &&
+           (depth == 0 || depth == 2 || depth == 3);
+}
+
+template <int RULE, int W4, int NS>
+static cudaError_t fused_rule(const uint32_t *cur, uint32_t *nxt, int L, int R, uint64_t seed, int mixed, uint32_t t,
+                              int TZ, cudaStream_t s)
+{
+    constexpr size_t smem = fused_smem_bytes<W4, NS>();
+    cudaError_t e =
+        cudaFuncSetAttribute(k_mcs_fused<RULE, W4, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)  // shared memory for 3 CTAs per SM (the rest stays L1)
+        e = cudaFuncSetAttribute(k_mcs_fused<RULE, W4, NS>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+    const Geom g = make_geom(L);
+    constexpr int TY = 256 / W4;
+    const dim3 grid((unsigned)((L / TY) * (L / TZ)), (unsigned)R);
+    k_mcs_fused<RULE, W4, NS><<<grid, 256, smem, s>>>(cur, nxt, g, mixed, t, seed, TZ);
+    return cudaGetLastError();
+}
+
+template <int RULE, int NS>
+static cudaError_t fused_one(const uint32_t *cur, uint32_t *nxt, int L, int R, uint64_t seed, int mixed, uint32_t t,
+                             int TZ, cudaStream_t s)
+{
+    switch (L / 256) {
+    case 1: return fused_rule<RULE, 1, NS>(cur, nxt, L, R, seed, mixed, t, TZ, s);
+    case 2: return fused_rule<RULE, 2, NS>(cur, nxt, L, R, seed, mixed, t, TZ, s);
+    case 4: return fused_rule<RULE, 4, NS>(cur, nxt, L, R, seed, mixed, t, TZ, s);
+    case 8: return fused_rule<RULE, 8, NS>(cur, nxt, L, R, seed, mixed, t, TZ, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+// depth = copy groups in flight while a step computes: 2 (five slots) or 3 (six)
+template <int RULE>
+static cudaError_t fused_depth(const uint32_t *cur, uint32_t *nxt, int L, int R, uint64_t seed, int mixed,
+                               uint32_t t, int TZ, int depth, cudaStream_t s)
+{
+    return depth == 3 ? fused_one<RULE, 6>(cur, nxt, L, R, seed, mixed, t, TZ, s)
+                      : fused_one<RULE, 5>(cur, nxt, L, R, seed, mixed, t, TZ, s);
+}
+
+cudaError_t launch_sweeps_fused(uint32_t **cur, uint32_t **nxt, int L, int R, uint64_t seed, int rule, int64_t t0,
+                                int64_t n_mcs, int cycle, int TZ, int depth, cudaStream_t s, int64_t *launches)
+{
+    for (int64_t k = 0; k < n_mcs; ++k) {
+        const uint32_t t = (uint32_t)(t0 + k);
+        cudaError_t e;
+        switch (rule) {
+        case TIE_GLAUBER: e = fused_depth<TIE_GLAUBER>(*cur, *nxt, L, R, seed, cycle, t, TZ, depth, s); break;
+        case TIE_ALWAYS: e = fused_depth<TIE_ALWAYS>(*cur, *nxt, L, R, seed, cycle, t, TZ, depth, s); break;
+        default: e = fused_depth<TIE_NEVER>(*cur, *nxt, L, R, seed, cycle, t, TZ, depth, s); break;
+        }
+        if (e != cudaSuccess) return e;
+        uint32_t *tmp = *cur;  // the new sweep becomes the current store
+        *cur = *nxt;
+        *nxt = tmp;
+        if (launches) ++*launches;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace ising

@@ -459,6 +459,7 @@ static bool zfast_width_ok(int L) { return L % 256 == 0 && (L / 256 == 1 || L / 
 bool sweep_config_valid(int L, const SweepConfig &c)
 {
     if (c.variant == VARIANT_WORD) return true;
+    if (c.variant == VARIANT_ZFUSE) return fused_config_valid(L, c.tile_z, c.depth);
     if (c.variant == VARIANT_ZFAST)
         return L >= 256 && zfast_width_ok(L) && c.tile_z >= 1 && L % c.tile_z == 0 && L % (256 / (L / 256)) == 0;
     if (c.variant == VARIANT_ZDEEP)
@@ -505,6 +506,7 @@ static cudaError_t half_sweep_rule(uint32_t *lat, int L, int R, uint64_t seed, i
                                    const SweepConfig &cfg, cudaStream_t s)
 {
     const Geom g = make_geom(L);
+    if (cfg.variant == VARIANT_ZFUSE) return cudaErrorInvalidValue;  // needs two stores: launch_sweeps_fused
     if (cfg.variant == VARIANT_ZDEEP) {
         const int W4 = L / 256;
         const dim3 grid((unsigned)((L / (256 / W4)) * (L / cfg.tile_z)), (unsigned)R);

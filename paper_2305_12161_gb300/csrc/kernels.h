@@ -18,6 +18,7 @@ enum SweepVariant : int {
     VARIANT_ZMARCH = 2,  // z-marching, cp.async-staged tiles, 128 spins per thread, L >= 256
     VARIANT_ZFAST = 3,   // z-marching specialised on the row width (L = 256, 512, 1024, 2048)
     VARIANT_ZDEEP = 4,   // as ZFAST with a deeper copy pipeline (depth 2..4) and fewer registers
+    VARIANT_ZFUSE = 5,   // one launch per sweep (both sublattices), ping-pong between two stores
 };
 
 struct SweepConfig {
@@ -29,6 +30,13 @@ struct SweepConfig {
 
 bool sweep_config_valid(int L, const SweepConfig &c);
 SweepConfig default_sweep_config(int L, int R);
+
+// Fused sweeps (VARIANT_ZFUSE): each sweep reads *cur and writes *nxt, then swaps the two
+// pointers, so after n sweeps *cur holds the state.  Both stores hold 2*R*nw words.
+// depth: copy groups in flight while a step computes, 2 or 3 (0 = 2; SweepConfig.depth).
+bool fused_config_valid(int L, int tile_z, int depth);
+cudaError_t launch_sweeps_fused(uint32_t **cur, uint32_t **nxt, int L, int R, uint64_t seed, int rule, int64_t t0,
+                                int64_t n_mcs, int cycle, int tile_z, int depth, cudaStream_t s, int64_t *launches);
 
 // n_mcs sweeps from completed-sweep count t0; returns the number of launches through
 // *launches.

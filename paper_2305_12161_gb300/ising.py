@@ -30,7 +30,7 @@ CYCLE_01, CYCLE_MIXED = 0, 1
 CORR_AUTO, CORR_POPCOUNT, CORR_TENSOR = 0, 1, 2
 SCHEME_CHECKERBOARD, SCHEME_DOUBLE = 0, 1
 FFT_SINGLE, FFT_DOUBLE = 0, 1
-VARIANT_AUTO, VARIANT_WORD, VARIANT_ZMARCH, VARIANT_ZFAST, VARIANT_ZDEEP = 0, 1, 2, 3, 4
+VARIANT_AUTO, VARIANT_WORD, VARIANT_ZMARCH, VARIANT_ZFAST, VARIANT_ZDEEP, VARIANT_ZFUSE = 0, 1, 2, 3, 4, 5
 
 
 class IsingError(RuntimeError):

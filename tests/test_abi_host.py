@@ -54,7 +54,7 @@ def test_strerror_and_variants(lib):
     for code in range(0, -7, -1):
         assert isinstance(ising.ising_strerror(code), str) and ising.ising_strerror(code)
     assert ising.ising_variants() == [ising.VARIANT_WORD, ising.VARIANT_ZMARCH, ising.VARIANT_ZFAST,
-                                     ising.VARIANT_ZDEEP]
+                                     ising.VARIANT_ZDEEP, ising.VARIANT_ZFUSE]
 
 
 def test_create_rejects_bad_arguments_before_touching_a_device(lib):

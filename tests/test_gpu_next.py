@@ -36,7 +36,7 @@ def test_menger_start_and_quench(ising, L, k, form):
             assert np.array_equal(rec[r], oracle.record(s, 4))
 
 
-@pytest.mark.parametrize("variant,L", [(1, 16), (1, 64), (3, 256), (4, 256), (2, 256)])
+@pytest.mark.parametrize("variant,L", [(1, 16), (1, 64), (3, 256), (4, 256), (2, 256), (5, 256)])
 def test_mixed_cycle_vs_oracle(ising, variant, L):
     R, seed = 3, 21
     with ising.Ising(L, replicas=R, seed=seed, variant=variant, cycle=ising.CYCLE_MIXED) as q:

@@ -95,6 +95,20 @@ def test_zfast_rules_and_replicas_L256(ising):
     _compare(ising, 256, 2, 21, [2], variant=ising.VARIANT_ZFAST, tile_z=8)
 
 
+@pytest.mark.parametrize("tz", [1, 4, 16, 256])
+def test_zfuse_L256_vs_oracle(ising, tz):
+    # odd and even sweep counts: the state ends in either of the two stores
+    _compare(ising, 256, 1, 16, [1, 2, 5], variant=ising.VARIANT_ZFUSE, tile_z=tz)
+
+
+def test_zfuse_rules_and_replicas_L256(ising):
+    for rule in (1, 2):
+        _compare(ising, 256, 1, 17, [1, 3], rule=rule, variant=ising.VARIANT_ZFUSE, tile_z=32)
+    _compare(ising, 256, 3, 22, [3], variant=ising.VARIANT_ZFUSE, tile_z=8)
+    # three copy groups in flight
+    _compare(ising, 256, 2, 23, [1, 4], variant=ising.VARIANT_ZFUSE, tile_z=16, depth=3)
+
+
 def test_zmarch_rules_L256(ising):
     for rule in (1, 2):
         _compare(ising, 256, 1, 5, [1, 3], rule=rule, variant=ising.VARIANT_ZMARCH)
@@ -128,6 +142,19 @@ def test_variants_and_tiles_bit_identical(ising, L):
             got, grec = _packed_state(ising, L, 1, 9, 6, variant=ising.VARIANT_ZDEEP, tile_z=tz, depth=d)
             assert np.array_equal(got[0], ref[0]), ("zdeep", tz, d)
             assert np.array_equal(grec, rec)
+    for tz in (1, 16, 64, L):
+        got, grec = _packed_state(ising, L, 1, 9, 6, variant=ising.VARIANT_ZFUSE, tile_z=tz)
+        assert np.array_equal(got[0], ref[0]), ("zfuse", tz)
+        assert np.array_equal(grec, rec)
+
+
+@pytest.mark.parametrize("rule", RULES)
+def test_zfuse_matches_zfast_L512_rules_replicas_odd_count(ising, rule):
+    ref, rec = _packed_state(ising, 512, 2, 31, 7, tie=rule, variant=ising.VARIANT_ZFAST)
+    got, grec = _packed_state(ising, 512, 2, 31, 7, tie=rule, variant=ising.VARIANT_ZFUSE, tile_z=32)
+    for r in range(2):
+        assert np.array_equal(got[r], ref[r]), r
+    assert np.array_equal(grec, rec)
 
 
 def test_plain_and_packed_forms_identical_L256(ising):
