@@ -486,6 +486,7 @@ def main():
     q = ising.Ising(L, replicas=1, seed=seed, stream=stream, variant=tuned["variant"], tile_y=tuned["tile_y"],
                     tile_z=tuned["tile_z"], depth=tuned["depth"], corr=args.corr)
     RL = q.record_len
+    per_mcs = 1 if tuned["variant"] == 5 else 2  # sweep kernel launches per MCS
     offsets = inputs.log_schedule(MCS, K)
     nwords = ising.ising_packed_words(L)
 
@@ -539,7 +540,7 @@ def main():
                     q.measure_device(rec_dev[leg, k], der_dev[leg, k], c=0.5)
                 c = ev() if timing else None
                 if timing:
-                    sweep_events.append((a, b, 2 * (off - (offsets[k - 1] if k else 0)), leg))
+                    sweep_events.append((a, b, per_mcs * (off - (offsets[k - 1] if k else 0)), leg))
                     meas_events.append((b, c))
         return outs
 

@@ -76,7 +76,8 @@ typedef struct {
                        4 as 3 with a deeper copy pipeline and fewer registers,
                        5 one launch per sweep updating both sublattices (L = 256 .. 2048, powers
                          of two; holds a second packed store of the same size, the two swap
-                         roles every sweep) */
+                         roles every sweep, so a CUDA graph captured around ising_sweep replays
+                         correctly only for an even sweep count) */
     int tile_y;     /* packed z-marching variant: rows per tile (0 = automatic); variant 3
                        (z-marching specialised on the row width) fixes it to 256/(L/256) */
     int tile_z;     /* packed z-marching variants: planes per tile (0 = automatic) */
