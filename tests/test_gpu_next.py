@@ -36,10 +36,11 @@ def test_menger_start_and_quench(ising, L, k, form):
             assert np.array_equal(rec[r], oracle.record(s, 4))
 
 
-@pytest.mark.parametrize("variant,L", [(1, 16), (1, 64), (3, 256), (4, 256), (2, 256), (5, 256)])
-def test_mixed_cycle_vs_oracle(ising, variant, L):
+@pytest.mark.parametrize("variant,L,depth", [(1, 16, 0), (1, 64, 0), (3, 256, 0), (4, 256, 0), (2, 256, 0),
+                                             (5, 256, 0), (5, 256, 11)])
+def test_mixed_cycle_vs_oracle(ising, variant, L, depth):
     R, seed = 3, 21
-    with ising.Ising(L, replicas=R, seed=seed, variant=variant, cycle=ising.CYCLE_MIXED) as q:
+    with ising.Ising(L, replicas=R, seed=seed, variant=variant, depth=depth, cycle=ising.CYCLE_MIXED) as q:
         q.sweep(5)
         rec = q.measure()
         for r in range(R):

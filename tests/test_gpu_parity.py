@@ -101,6 +101,13 @@ def test_zfuse_L256_vs_oracle(ising, tz):
     _compare(ising, 256, 1, 16, [1, 2, 5], variant=ising.VARIANT_ZFUSE, tile_z=tz)
 
 
+@pytest.mark.parametrize("tz", [1, 8, 256])
+def test_zfuse_balanced_L256_vs_oracle(ising, tz):
+    # 254-row tiles: the second of the two tiles owns two rows and wraps onto the first
+    _compare(ising, 256, 1, 18, [1, 2, 5], variant=ising.VARIANT_ZFUSE, tile_z=tz, depth=11)
+    _compare(ising, 256, 2, 19, [3], rule=1, variant=ising.VARIANT_ZFUSE, tile_z=tz, depth=8)
+
+
 def test_zfuse_rules_and_replicas_L256(ising):
     for rule in (1, 2):
         _compare(ising, 256, 1, 17, [1, 3], rule=rule, variant=ising.VARIANT_ZFUSE, tile_z=32)
@@ -143,18 +150,20 @@ def test_variants_and_tiles_bit_identical(ising, L):
             assert np.array_equal(got[0], ref[0]), ("zdeep", tz, d)
             assert np.array_equal(grec, rec)
     for tz in (1, 16, 64, L):
-        got, grec = _packed_state(ising, L, 1, 9, 6, variant=ising.VARIANT_ZFUSE, tile_z=tz)
-        assert np.array_equal(got[0], ref[0]), ("zfuse", tz)
-        assert np.array_equal(grec, rec)
+        for d in (0, 11):  # ragged tiles of 256 / W4 - 2 rows in the balanced form
+            got, grec = _packed_state(ising, L, 1, 9, 6, variant=ising.VARIANT_ZFUSE, tile_z=tz, depth=d)
+            assert np.array_equal(got[0], ref[0]), ("zfuse", tz, d)
+            assert np.array_equal(grec, rec)
 
 
 @pytest.mark.parametrize("rule", RULES)
 def test_zfuse_matches_zfast_L512_rules_replicas_odd_count(ising, rule):
     ref, rec = _packed_state(ising, 512, 2, 31, 7, tie=rule, variant=ising.VARIANT_ZFAST)
-    got, grec = _packed_state(ising, 512, 2, 31, 7, tie=rule, variant=ising.VARIANT_ZFUSE, tile_z=32)
-    for r in range(2):
-        assert np.array_equal(got[r], ref[r]), r
-    assert np.array_equal(grec, rec)
+    for d in (0, 10):
+        got, grec = _packed_state(ising, 512, 2, 31, 7, tie=rule, variant=ising.VARIANT_ZFUSE, tile_z=32, depth=d)
+        for r in range(2):
+            assert np.array_equal(got[r], ref[r]), (r, d)
+        assert np.array_equal(grec, rec)
 
 
 def test_plain_and_packed_forms_identical_L256(ising):
