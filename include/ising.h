@@ -353,8 +353,10 @@ int ising_measure_derived_noalloc(const uint32_t *lattice, int L, int replicas, 
  * probe_mcs sweeps (after 2 warm-up sweeps) of every valid kernel variant and tile
  * shape (tile_y rows x tile_z planes per CTA; tile_z sets how many 128-spin words each
  * thread updates per launch), on scratch contexts built from *base (NULL: defaults),
- * and writes the fastest options to *best (and its time per MCS in ms).  All
- * candidates give bit-identical results, so the choice affects speed only. */
+ * and writes the fastest options to *best (and its time per MCS in ms).  Variant 5
+ * holds a second packed store, so it is chosen only when it beats the fastest
+ * single-store candidate by more than 3%.  All candidates give bit-identical results,
+ * so the choice affects speed and memory only. */
 int ising_tune_sweep(int L, int replicas, int probe_mcs, const ising_opts *base, ising_opts *best,
                      double *best_ms_per_mcs);
 
