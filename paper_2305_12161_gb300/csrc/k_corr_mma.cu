@@ -88,9 +88,8 @@ __device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity, uint64
 // contiguous KB (rows L^2 bytes apart would put every box's rows at a large power-of-two
 // stride).  Column cc of the panels (32 lines) is K = 32 cc .. 32 cc + 31.  Every word of the
 // lattice is expanded once instead of once per tile pair.
-__device__ __forceinline__ void store_e4m3_word(uint8_t *dst, uint32_t v)
+__device__ __forceinline__ void expand_e4m3_word(uint32_t v, uint4 &lo, uint4 &hi)
 {
-    uint4 lo, hi;
     lo.x = e4m3x4(v & 0xFu);
     lo.y = e4m3x4((v >> 4) & 0xFu);
     lo.z = e4m3x4((v >> 8) & 0xFu);
@@ -99,17 +98,26 @@ __device__ __forceinline__ void store_e4m3_word(uint8_t *dst, uint32_t v)
     hi.y = e4m3x4((v >> 20) & 0xFu);
     hi.z = e4m3x4((v >> 24) & 0xFu);
     hi.w = e4m3x4(v >> 28);
+}
+
+__device__ __forceinline__ void store_e4m3_word(uint8_t *dst, uint32_t v)
+{
+    uint4 lo, hi;
+    expand_e4m3_word(v, lo, hi);
     reinterpret_cast<uint4 *>(dst)[0] = lo;
     reinterpret_cast<uint4 *>(dst)[1] = hi;
 }
 
 // x axis, straight from the packed store: a CTA stages both sublattices' words of 128
 // consecutive rows (row = y + L z; four bundles B of 32 rows) in shared memory with coalesced
-// loads; a warp then takes the words kw of sublattice-parity class pi of those rows (lane =
-// row in the bundle), transposes each 32 x 32 bit block in registers (five shuffle stages, each
+// loads; a warp then takes word column kw of both parity classes pi of those rows (lane = row
+// in the bundle), transposes each 32 x 32 bit block in registers (five shuffle stages, each
 // swapping the off-diagonal half-blocks of size j between lanes r and r ^ j), after which lane
-// i holds, for site x = 2 (32 kw + i) + pi, the bits of the bundle's 32 rows; the four bundles
-// fill position x's 128-byte line of the chunk.
+// i holds, for site x = 2 (32 kw + i) + pi, the bits of the bundle's 32 rows.  The 64
+// positions x = 64 kw .. 64 kw + 63 of the column are consecutive 128-byte lines of the chunk:
+// the warp expands them into shared memory (16-byte piece c of position P at piece
+// c ^ ((P >> 1) & 7), so both the scattered writes and the line-ordered reads are
+// conflict-free) and writes the 8 KB with 512-byte coalesced stores.
 __device__ __forceinline__ uint32_t transpose32_lane(uint32_t v, int lane)
 {
     const uint32_t FULL = 0xffffffffu;
@@ -124,11 +132,14 @@ __device__ __forceinline__ uint32_t transpose32_lane(uint32_t v, int lane)
     return v;
 }
 
+static size_t expand_x_smem_bytes(int W) { return (size_t)128 * (2 * W + 1) * sizeof(uint32_t) + 8 * 64 * 128; }
+
 __global__ void __launch_bounds__(256) k_expand_x_e4m3(const uint32_t *S0, const uint32_t *S1, Geom g, uint8_t *E)
 {
-    extern __shared__ uint32_t xt[];  // [128 rows][2 W + 1]: both sublattices' words of a row
+    extern __shared__ __align__(16) uint32_t xt[];  // [128 rows][2 W + 1], then 8 warps x [64 lines][128 B]
     const int L = g.L, W = g.W, RS = 2 * W + 1;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint4 *lines = reinterpret_cast<uint4 *>(xt + 128 * RS) + warp * 64 * 8;
     const int64_t nB4 = (int64_t)L * L / 128;  // chunks of 128 rows = 4 bundles of 32
     const int64_t blk = (int64_t)L * GT_KB;
     for (int64_t B4 = blockIdx.x; B4 < nB4; B4 += gridDim.x) {
@@ -140,18 +151,30 @@ __global__ void __launch_bounds__(256) k_expand_x_e4m3(const uint32_t *S0, const
             xt[ri * RS + c] = __ldg((sub ? S1 : S0) + (128 * B4 + ri) * W + kw);
         }
         __syncthreads();
-        for (int task = warp; task < 2 * W; task += blockDim.x / 32) {
-            const int pi = task / W, kw = task - pi * W;
-            const int x = 2 * (32 * kw + lane) + pi;
-            uint8_t *dst = E + B4 * blk + (int64_t)x * GT_KB;  // one full 128-byte line per lane
+        for (int kw = warp; kw < W; kw += blockDim.x / 32) {
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
                 const int ri = 32 * b + lane;
-                const int64_t row = 128 * B4 + ri;
-                const int y = (int)(row % L), z = (int)(row / L);
-                const uint32_t v = xt[ri * RS + (((pi + y + z) & 1) ? W : 0) + kw];
-                store_e4m3_word(dst + 32 * b, transpose32_lane(v, lane));
+                const uint32_t row = (uint32_t)(128 * B4 + ri);  // < L^2
+                const uint32_t z = row / (uint32_t)L, y = row - z * (uint32_t)L;
+#pragma unroll
+                for (int pi = 0; pi < 2; ++pi) {
+                    const uint32_t v = xt[ri * RS + (((pi + y + z) & 1u) ? W : 0) + kw];
+                    uint4 lo, hi;
+                    expand_e4m3_word(transpose32_lane(v, lane), lo, hi);
+                    const int P = 2 * lane + pi, sw = lane & 7;  // (P >> 1) & 7
+                    lines[P * 8 + ((2 * b) ^ sw)] = lo;
+                    lines[P * 8 + ((2 * b + 1) ^ sw)] = hi;
+                }
             }
+            __syncwarp();
+            uint4 *dst = reinterpret_cast<uint4 *>(E + B4 * blk + (int64_t)64 * kw * GT_KB);
+#pragma unroll 4
+            for (int j = 0; j < 16; ++j) {
+                const int t = 32 * j + lane, P = t >> 3;
+                dst[t] = lines[P * 8 + ((t & 7) ^ ((P >> 1) & 7))];
+            }
+            __syncwarp();
         }
     }
 }
@@ -397,13 +420,16 @@ cudaError_t launch_corr_mma(const uint32_t *lat, int L, int R, int64_t *rec, uin
     if (split < 1) split = 1;
     const int64_t H = L / 2, RL = 3 + 3 * (H + 1);
     const int ncols_e = (int)((int64_t)L * L / 32);
+    const size_t xsm = expand_x_smem_bytes(g.W);
+    if ((e = cudaFuncSetAttribute(k_expand_x_e4m3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsm)) !=
+        cudaSuccess)
+        return e;
     int64_t nl = 0;
     for (int r = 0; r < R; ++r) {
         const uint32_t *S0 = lat + 2 * (int64_t)r * g.nw;
         for (int axis = 0; axis < 3; ++axis) {
-            if (axis == 0) {  // 32 x 32 bit transposes, one warp per (bundle, parity, word)
-                const size_t xsm = (size_t)128 * (2 * g.W + 1) * sizeof(uint32_t);
-                k_expand_x_e4m3<<<(unsigned)std::min<int64_t>((int64_t)L * L / 128, (int64_t)sms * 4), 256, xsm, s>>>(
+            if (axis == 0) {  // 32 x 32 bit transposes, one warp per word column (both parities)
+                k_expand_x_e4m3<<<(unsigned)std::min<int64_t>((int64_t)L * L / 128, (int64_t)sms * 2), 256, xsm, s>>>(
                     S0, S0 + g.nw, g, E);
             } else {          // positions over grid.y, columns over the threads
                 const dim3 eg((unsigned)std::max(1, std::min(8, ncols_e / 256)), (unsigned)L);

@@ -83,6 +83,67 @@ __global__ void k_mb(const uint32_t *lat, Geom g, int64_t *rec)
     }
 }
 
+// The same counts for L a multiple of 256: one thread per uint4 of sublattice 0 (128 sites of
+// one row), rows found with 32-bit divisions (L^3 / 256 < 2^32) instead of 64-bit ones.
+__global__ void k_mb4(const uint32_t *lat, Geom g, int64_t *rec)
+{
+    const int r = blockIdx.y;
+    const uint4 *S0 = reinterpret_cast<const uint4 *>(lat + (2 * (int64_t)r) * g.nw);
+    const uint4 *S1 = S0 + g.nw / 4;
+    const uint32_t L = (uint32_t)g.L, W4 = L / 256, n4 = (uint32_t)(g.nw / 4);
+    long long m = 0, b = 0;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += gridDim.x * blockDim.x) {
+        const uint32_t row = i / W4, cx = i - row * W4;
+        const uint32_t z = row / L, y = row - z * L;
+        const uint4 s = __ldg(S0 + i);
+        const uint4 C = __ldg(S1 + i);
+        // x-neighbours that are not C itself: shifted by one site towards x - 1 (p = 0) or x + 1
+        uint4 X;
+        if (((y + z) & 1u) == 0) {
+            const uint32_t e = __ldg(reinterpret_cast<const uint32_t *>(S1 + row * W4 + (cx == 0 ? W4 - 1 : cx - 1)) + 3);
+            X = make_uint4((C.x << 1) | (e >> 31), (C.y << 1) | (C.x >> 31), (C.z << 1) | (C.y >> 31),
+                           (C.w << 1) | (C.z >> 31));
+        } else {
+            const uint32_t e = __ldg(reinterpret_cast<const uint32_t *>(S1 + row * W4 + (cx == W4 - 1 ? 0 : cx + 1)));
+            X = make_uint4((C.x >> 1) | (C.y << 31), (C.y >> 1) | (C.z << 31), (C.z >> 1) | (C.w << 31),
+                           (C.w >> 1) | (e << 31));
+        }
+        const uint32_t ym = y == 0 ? L - 1 : y - 1, yp = y == L - 1 ? 0 : y + 1;
+        const uint32_t zm = z == 0 ? L - 1 : z - 1, zp = z == L - 1 ? 0 : z + 1;
+        const uint4 Ym = __ldg(S1 + (z * L + ym) * W4 + cx), Yp = __ldg(S1 + (z * L + yp) * W4 + cx);
+        const uint4 Zm = __ldg(S1 + (zm * L + y) * W4 + cx), Zp = __ldg(S1 + (zp * L + y) * W4 + cx);
+        auto bonds = [&](uint32_t sw, uint32_t c, uint32_t x, uint32_t a, uint32_t bb, uint32_t d, uint32_t e) {
+            return __popc(sw ^ c) + __popc(sw ^ x) + __popc(sw ^ a) + __popc(sw ^ bb) + __popc(sw ^ d) + __popc(sw ^ e);
+        };
+        b += bonds(s.x, C.x, X.x, Ym.x, Yp.x, Zm.x, Zp.x) + bonds(s.y, C.y, X.y, Ym.y, Yp.y, Zm.y, Zp.y) +
+             bonds(s.z, C.z, X.z, Ym.z, Yp.z, Zm.z, Zp.z) + bonds(s.w, C.w, X.w, Ym.w, Yp.w, Zm.w, Zp.w);
+        m += 2 * (__popc(s.x) + __popc(s.y) + __popc(s.z) + __popc(s.w) + __popc(C.x) + __popc(C.y) + __popc(C.z) +
+                  __popc(C.w)) -
+             2 * 128;
+    }
+    __shared__ long long red[2][32];
+    m = warp_sum(m);
+    b = warp_sum(b);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        red[0][wid] = m;
+        red[1][wid] = b;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = blockDim.x >> 5;
+        m = lane < nw ? red[0][lane] : 0;
+        b = lane < nw ? red[1][lane] : 0;
+        m = warp_sum(m);
+        b = warp_sum(b);
+        if (lane == 0) {
+            const int64_t RL = rec_len(g.L);
+            atomicAdd(reinterpret_cast<unsigned long long *>(rec + r * RL + 1), (unsigned long long)m);
+            atomicAdd(reinterpret_cast<unsigned long long *>(rec + r * RL + 2), (unsigned long long)b);
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------------
 // Axis correlation.  blockIdx.z = axis (0 = x, 1 = y, 2 = z), blockIdx.y = replica,
 // blockIdx.x strides over panels of NC columns (a persistent grid).
@@ -346,9 +407,15 @@ cudaError_t launch_measure(const uint32_t *lat, int L, int R, int64_t t, int cor
     int64_t nb = (RL * R + 255) / 256;
     if (nb > 4096) nb = 4096;
     k_rec_init<<<(unsigned)nb, 256, 0, s>>>(rec, L, R, t, corr);
-    int64_t mb = (g.nw + 255) / 256;
-    if (mb > 152 * 8) mb = 152 * 8;
-    k_mb<<<dim3((unsigned)mb, (unsigned)R), 256, 0, s>>>(lat, g, rec);
+    if (L >= 256 && L % 256 == 0) {
+        int64_t mb = (g.nw / 4 + 255) / 256;
+        if (mb > 152 * 8) mb = 152 * 8;
+        k_mb4<<<dim3((unsigned)mb, (unsigned)R), 256, 0, s>>>(lat, g, rec);
+    } else {
+        int64_t mb = (g.nw + 255) / 256;
+        if (mb > 152 * 8) mb = 152 * 8;
+        k_mb<<<dim3((unsigned)mb, (unsigned)R), 256, 0, s>>>(lat, g, rec);
+    }
     int n = 2;
     if (corr == CORR_TENSOR) {
         if (!xt_scratch || !err || !corr_mma_supported(L)) return cudaErrorInvalidValue;
