@@ -497,7 +497,6 @@ def main():
     ck_host = torch.empty(nwords, dtype=torch.int32, pin_memory=True)
     q.sync()
     ck_host.copy_(ck_dev.cpu())
-    ck_host_np = ck_host.numpy().view(np.uint32)
     rec_dev = torch.empty((2, K, RL), dtype=torch.int64, device="cuda")
     der_dev = torch.empty((2, K, 4), dtype=torch.float64, device="cuda")
     torch.cuda.synchronize()
@@ -515,6 +514,10 @@ def main():
         e.record(stream)
         return e
 
+    # end-to-end leg: the step's results land in pinned host buffers (one read-back per step)
+    rec_host = torch.empty((2, K, RL), dtype=torch.int64, pin_memory=True)
+    der_host = torch.empty((2, K, 4), dtype=torch.float64, pin_memory=True)
+
     def step(e2e: bool, timing: bool):
         outs = []
         for leg in (0, 1):
@@ -522,8 +525,8 @@ def main():
                 q.reinit(seed)
                 t0 = 0
             else:
-                if e2e:
-                    q.set_packed(ck_host_np, 0)
+                if e2e:  # from pinned host memory; the transfer overlaps leg (i) on the device
+                    q.set_packed(ck_host, 0, asynchronous=True)
                 else:
                     q.set_packed(ck_dev, 0, device=True)
                 q.t = TCK
@@ -534,14 +537,17 @@ def main():
                 q.sweep(t0 + off - t)
                 b = ev() if timing else None
                 t = t0 + off
-                if e2e:
-                    outs.append(q.measure_ex(c=0.5))
-                else:
-                    q.measure_device(rec_dev[leg, k], der_dev[leg, k], c=0.5)
+                q.measure_device(rec_dev[leg, k], der_dev[leg, k], c=0.5)
                 c = ev() if timing else None
                 if timing:
                     sweep_events.append((a, b, per_mcs * (off - (offsets[k - 1] if k else 0)), leg))
                     meas_events.append((b, c))
+        if e2e:  # the device-to-host read of the step's records and derived quantities
+            with torch.cuda.stream(stream):
+                rec_host.copy_(rec_dev, non_blocking=True)
+                der_host.copy_(der_dev, non_blocking=True)
+            q.sync()
+            outs.append((rec_host, der_host))
         return outs
 
     def timed(e2e: bool, n: int):

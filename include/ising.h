@@ -199,8 +199,9 @@ int ising_measure_radial(ising_ctx *ctx, int replica, int precision, double cval
 int ising_inject_corr_stall(ising_ctx *ctx, double timeout_s);
 
 /* Free the scratch that measurements keep in the context (the radial measurement's transform
- * buffer and work area, the tensor-core correlation's transposed lattice); the next
- * measurement that needs it allocates it again.  Synchronises the context's stream. */
+ * buffer and work area, the tensor-core correlation's expanded lattice) and the staging
+ * buffer of asynchronous ising_set_packed; the next call that needs one allocates it again.
+ * Synchronises the context's streams. */
 int ising_release_scratch(ising_ctx *ctx);
 
 /* Number of int64 values of one replica's record:
@@ -234,6 +235,14 @@ int ising_set_spins(ising_ctx *ctx, int replica, const int8_t *host_in);
 
 /* Flags of the packed-state calls. */
 #define ISING_PTR_DEVICE 1u /* the buffer is device memory; no synchronisation */
+/* ising_set_packed only: the host buffer is page-locked (cudaHostAlloc / registered) and the
+ * caller keeps it alive and unchanged until ising_sync returns.  The call returns without
+ * waiting: the words go to a staging buffer of the context (one replica's packed size,
+ * allocated on first use, freed by ising_release_scratch or ising_destroy) on a copy stream
+ * of its own, so the transfer overlaps work already queued on the context's stream; that
+ * stream then waits for it and copies the staged words into the replica.  Ordering with the
+ * context's other calls is as for ISING_PTR_DEVICE. */
+#define ISING_PTR_HOST_ASYNC 2u
 
 /* Number of uint32 words of one replica's packed state (2 * ceil(N/64) style, see
  * below); -1 for bad L.  Layout: sublattice 0 then sublattice 1; within a sublattice,

@@ -25,6 +25,10 @@ struct ising_ctx {
     bool own_stream = false;
     uint32_t *lat = nullptr;     // packed store (PACKED form), or measurement copy (PLAIN form)
     uint32_t *lat_alt = nullptr; // second packed store of the fused sweep (VARIANT_ZFUSE)
+    uint32_t *stage = nullptr;   // staging of ising_set_packed(ISING_PTR_HOST_ASYNC), one replica
+    cudaStream_t copy_stream = nullptr;  // its host-to-device copies
+    cudaEvent_t staged = nullptr;        // the staged words have landed (copy stream)
+    cudaEvent_t stage_free = nullptr;    // the context stream has consumed them
     int8_t *plain = nullptr;     // PLAIN form lattice
     int64_t *rec_dev = nullptr;  // R records
     double *der_dev = nullptr;   // R x 4
@@ -164,6 +168,8 @@ int ising_destroy(ising_ctx *c)
         if (c->stream) {
             if (c->lat) cudaFreeAsync(c->lat, c->stream);
             if (c->lat_alt) cudaFreeAsync(c->lat_alt, c->stream);
+            if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
+            if (c->stage) cudaFreeAsync(c->stage, c->stream);
             if (c->plain) cudaFreeAsync(c->plain, c->stream);
             if (c->rec_dev) cudaFreeAsync(c->rec_dev, c->stream);
             if (c->der_dev) cudaFreeAsync(c->der_dev, c->stream);
@@ -174,6 +180,9 @@ int ising_destroy(ising_ctx *c)
             cudaStreamSynchronize(c->stream);
         }
         if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+        if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+        if (c->staged) cudaEventDestroy(c->staged);
+        if (c->stage_free) cudaEventDestroy(c->stage_free);
     }
     delete c;
     return ISING_OK;
@@ -417,6 +426,11 @@ int ising_release_scratch(ising_ctx *c)
     radial_release(c->radial, c->stream);
     if (c->xt) cudaFreeAsync(c->xt, c->stream);
     c->xt = nullptr;
+    if (c->stage) {  // the copy stream has finished with it before the context stream frees it
+        CK(c, cudaStreamSynchronize(c->copy_stream));
+        cudaFreeAsync(c->stage, c->stream);
+        c->stage = nullptr;
+    }
     CK(c, cudaStreamSynchronize(c->stream));
     return ISING_OK;
 }
@@ -556,9 +570,10 @@ int ising_set_packed(ising_ctx *c, int replica, const uint32_t *words, unsigned 
 {
     int s = check_ctx(c);
     if (s) return s;
-    if (!words || replica < 0 || replica >= c->R || (flags & ~ISING_PTR_DEVICE))
+    if (!words || replica < 0 || replica >= c->R || (flags & ~(ISING_PTR_DEVICE | ISING_PTR_HOST_ASYNC)) ||
+        flags == (ISING_PTR_DEVICE | ISING_PTR_HOST_ASYNC))
         return fail(c, ISING_EINVAL, "bad replica, buffer or flags");
-    const bool dev = flags & ISING_PTR_DEVICE;
+    const bool dev = flags & ISING_PTR_DEVICE, host_async = flags & ISING_PTR_HOST_ASYNC;
     if (!dev && c->L < 64) {
         const uint32_t m = row_mask(c->g.RB);
         for (int64_t i = 0; i < 2 * c->g.nw; ++i)
@@ -566,8 +581,31 @@ int ising_set_packed(ising_ctx *c, int replica, const uint32_t *words, unsigned 
     }
     DeviceGuard dg(c->device);
     const size_t bytes = 2 * (size_t)c->g.nw * sizeof(uint32_t);
-    CK(c, cudaMemcpyAsync(c->lat + (size_t)replica * 2 * c->g.nw, words, bytes,
-                          dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    if (host_async) {
+        if (!c->stage) {
+            if (cudaMallocAsync((void **)&c->stage, bytes, c->stream) != cudaSuccess) {
+                cudaGetLastError();
+                c->stage = nullptr;
+                return fail(c, ISING_ENOMEM, "staging buffer of %zu bytes", bytes);
+            }
+            if (!c->copy_stream) CK(c, cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+            if (!c->staged) CK(c, cudaEventCreateWithFlags(&c->staged, cudaEventDisableTiming));
+            if (!c->stage_free) CK(c, cudaEventCreateWithFlags(&c->stage_free, cudaEventDisableTiming));
+            CK(c, cudaEventRecord(c->stage_free, c->stream));  // the allocation is stream-ordered
+        }
+        // the copy stream waits only for the previous staged words to be consumed, not for
+        // the work queued on the context's stream
+        CK(c, cudaStreamWaitEvent(c->copy_stream, c->stage_free, 0));
+        CK(c, cudaMemcpyAsync(c->stage, words, bytes, cudaMemcpyHostToDevice, c->copy_stream));
+        CK(c, cudaEventRecord(c->staged, c->copy_stream));
+        CK(c, cudaStreamWaitEvent(c->stream, c->staged, 0));
+        CK(c, cudaMemcpyAsync(c->lat + (size_t)replica * 2 * c->g.nw, c->stage, bytes, cudaMemcpyDeviceToDevice,
+                              c->stream));
+        CK(c, cudaEventRecord(c->stage_free, c->stream));
+    } else {
+        CK(c, cudaMemcpyAsync(c->lat + (size_t)replica * 2 * c->g.nw, words, bytes,
+                              dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    }
     if (c->opts.form == ISING_FORM_PLAIN) {
         // expand only this replica into the byte lattice
         const size_t N = (size_t)c->L * c->L * c->L;
@@ -575,7 +613,7 @@ int ising_set_packed(ising_ctx *c, int replica, const uint32_t *words, unsigned 
                             c->stream));
         c->launches += 1;
     }
-    if (!dev) CK(c, cudaStreamSynchronize(c->stream));
+    if (!dev && !host_async) CK(c, cudaStreamSynchronize(c->stream));
     return ISING_OK;
 }
 

@@ -26,6 +26,7 @@ TIE_GLAUBER, TIE_ALWAYS, TIE_NEVER = 0, 1, 2
 FORM_PACKED, FORM_PLAIN = 0, 1
 MEAS_DEVICE, MEAS_CONNECTED, MEAS_NO_CORR = 1, 2, 4
 PTR_DEVICE = 1
+PTR_HOST_ASYNC = 2
 CYCLE_01, CYCLE_MIXED = 0, 1
 CORR_AUTO, CORR_POPCOUNT, CORR_TENSOR = 0, 1, 2
 SCHEME_CHECKERBOARD, SCHEME_DOUBLE = 0, 1
@@ -286,9 +287,20 @@ class Ising:
         self._check(lib().ising_get_packed(self._h, replica, out.ctypes.data, 0), "ising_get_packed")
         return out
 
-    def set_packed(self, words, replica: int = 0, device: bool = False) -> None:
+    def set_packed(self, words, replica: int = 0, device: bool = False, asynchronous: bool = False) -> None:
+        """Load one replica's packed words.  asynchronous=True: `words` is a page-locked host
+        torch tensor (pin_memory) that must stay alive and unchanged until sync(); the call
+        returns at once and the transfer overlaps the work already queued."""
         if device:
             self._check(lib().ising_set_packed(self._h, replica, _dev_ptr(words), PTR_DEVICE), "ising_set_packed")
+            return
+        if asynchronous:
+            if not (hasattr(words, "is_pinned") and words.is_pinned()):
+                raise ValueError("asynchronous set_packed needs a page-locked (pinned) torch tensor")
+            if words.numel() * words.element_size() != 4 * ising_packed_words(self.L) or not words.is_contiguous():
+                raise ValueError("words: one replica's packed state, contiguous")
+            self._check(lib().ising_set_packed(self._h, replica, ctypes.c_void_p(words.data_ptr()), PTR_HOST_ASYNC),
+                        "ising_set_packed")
             return
         w = _host(words, np.uint32, ising_packed_words(self.L), "words")
         self._check(lib().ising_set_packed(self._h, replica, w.ctypes.data, 0), "ising_set_packed")

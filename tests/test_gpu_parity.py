@@ -220,6 +220,43 @@ def test_checkpoint_resume_is_bit_exact(ising):
         assert np.array_equal(b.get_packed(0), end_a)
 
 
+@pytest.mark.parametrize("variant", [3, 5])
+def test_checkpoint_async_host_load_is_ordered(ising, variant):
+    # asynchronous loads from pinned memory land in stream order: queued sweeps run on the old
+    # state first, later sweeps on the loaded one; two loads in a row reuse the staging buffer
+    import torch
+    L = 256
+    with ising.Ising(L, replicas=2, seed=17) as a:
+        a.sweep(4)
+        w0, w1 = a.get_packed(0), a.get_packed(1)
+    p0 = torch.from_numpy(w0.view(np.int32).copy()).pin_memory()
+    p1 = torch.from_numpy(w1.view(np.int32).copy()).pin_memory()
+    with ising.Ising(L, replicas=2, seed=5, variant=variant) as ref:  # the synchronous path
+        ref.sweep(3)
+        ref.set_packed(w1, 0)
+        ref.set_packed(w0, 1)
+        ref.sweep(2)
+        ref.set_packed(w0, 0)
+        ref.sweep(3)
+        want = [ref.get_packed(0), ref.get_packed(1)]
+    with ising.Ising(L, replicas=2, seed=5, variant=variant) as q:
+        q.sweep(3)
+        q.set_packed(p1, 0, asynchronous=True)
+        q.set_packed(p0, 1, asynchronous=True)
+        q.sweep(2)
+        q.set_packed(p0, 0, asynchronous=True)
+        q.sweep(3)
+        q.sync()
+        assert np.array_equal(q.get_packed(0), want[0])
+        assert np.array_equal(q.get_packed(1), want[1])
+        with pytest.raises(ValueError):
+            q.set_packed(w0, 0, asynchronous=True)  # not page-locked
+        q.release_scratch()  # frees the staging buffer; the next load allocates it again
+        q.set_packed(p1, 1, asynchronous=True)
+        q.sync()
+        assert np.array_equal(q.get_packed(1), w1)
+
+
 def test_invalid_spin_values_rejected(ising):
     with ising.Ising(8, replicas=1, seed=1) as q:
         bad = np.ones((8, 8, 8), dtype=np.int8)
