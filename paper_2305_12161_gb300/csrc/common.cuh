@@ -174,6 +174,57 @@ __device__ __forceinline__ uint32_t resolve(uint32_t s, uint32_t ge4, uint32_t e
     return ge4 | (eq3 & tie);
 }
 
+__device__ __forceinline__ uint32_t maj3(uint32_t a, uint32_t b, uint32_t c) { return (a & b) | (c & (a ^ b)); }
+
+// New spins of the 128 sites of one uint4 (T -> 0 Glauber, Eq. 6).  With u the number of up
+// neighbours and tau the tie bit (the old spin for the rule that never flips at zero energy,
+// its complement for the rule that always flips, the old spin xor the random bit for Glauber),
+// the new spin is [u + tau >= 4]: up where u >= 4, tau where u = 3, down where u <= 2.  Two
+// full adders give u = s1 + s2 + 2 (c1 + c2); a third adds s1 + s2 + tau = s3 + 2 c3, so the
+// new spin is the majority of c1, c2, c3.  Glauber draws Philox only where some site of the
+// group has u = 3, i.e. s1 != s2 and c1 != c2.  For Glauber, COMPACT first reduces the adders
+// to the masks [u >= 4] and [u = 3] (count6), which keeps two words per word live across the
+// Philox call instead of four, at one more logic operation per word.
+template <int RULE, bool COMPACT = true>
+__device__ __forceinline__ uint4 new_spins4(const uint4 &s, const uint4 &C, const uint4 &X, const uint4 &ym,
+                                            const uint4 &yp, const uint4 &zm, const uint4 &zp, uint32_t group,
+                                            uint32_t t, uint32_t q, const PhiloxKeys &keys)
+{
+    if (RULE == TIE_GLAUBER && COMPACT) {
+        uint32_t g0, g1, g2, g3, e0, e1, e2, e3;
+        count6(C.x, X.x, ym.x, yp.x, zm.x, zp.x, g0, e0);
+        count6(C.y, X.y, ym.y, yp.y, zm.y, zp.y, g1, e1);
+        count6(C.z, X.z, ym.z, yp.z, zm.z, zp.z, g2, e2);
+        count6(C.w, X.w, ym.w, yp.w, zm.w, zp.w, g3, e3);
+        U4 o{0u, 0u, 0u, 0u};
+        if ((e0 | e1 | e2 | e3) != 0u) o = philox4x32_10_rk(group, t, q, 0u, keys);
+        return make_uint4(resolve<RULE>(s.x, g0, e0, o.x), resolve<RULE>(s.y, g1, e1, o.y),
+                          resolve<RULE>(s.z, g2, e2, o.z), resolve<RULE>(s.w, g3, e3, o.w));
+    }
+    const uint32_t s1x = C.x ^ X.x ^ ym.x, c1x = maj3(C.x, X.x, ym.x);
+    const uint32_t s1y = C.y ^ X.y ^ ym.y, c1y = maj3(C.y, X.y, ym.y);
+    const uint32_t s1z = C.z ^ X.z ^ ym.z, c1z = maj3(C.z, X.z, ym.z);
+    const uint32_t s1w = C.w ^ X.w ^ ym.w, c1w = maj3(C.w, X.w, ym.w);
+    const uint32_t s2x = yp.x ^ zm.x ^ zp.x, c2x = maj3(yp.x, zm.x, zp.x);
+    const uint32_t s2y = yp.y ^ zm.y ^ zp.y, c2y = maj3(yp.y, zm.y, zp.y);
+    const uint32_t s2z = yp.z ^ zm.z ^ zp.z, c2z = maj3(yp.z, zm.z, zp.z);
+    const uint32_t s2w = yp.w ^ zm.w ^ zp.w, c2w = maj3(yp.w, zm.w, zp.w);
+    uint4 tau;
+    if (RULE == TIE_GLAUBER) {
+        const uint32_t tie = ((s1x ^ s2x) & (c1x ^ c2x)) | ((s1y ^ s2y) & (c1y ^ c2y)) |
+                             ((s1z ^ s2z) & (c1z ^ c2z)) | ((s1w ^ s2w) & (c1w ^ c2w));
+        U4 o{0u, 0u, 0u, 0u};
+        if (tie != 0u) o = philox4x32_10_rk(group, t, q, 0u, keys);
+        tau = make_uint4(s.x ^ o.x, s.y ^ o.y, s.z ^ o.z, s.w ^ o.w);
+    } else if (RULE == TIE_ALWAYS) {
+        tau = make_uint4(~s.x, ~s.y, ~s.z, ~s.w);
+    } else {
+        tau = s;
+    }
+    return make_uint4(maj3(c1x, c2x, maj3(s1x, s2x, tau.x)), maj3(c1y, c2y, maj3(s1y, s2y, tau.y)),
+                      maj3(c1z, c2z, maj3(s1z, s2z, tau.z)), maj3(c1w, c2w, maj3(s1w, s2w, tau.w)));
+}
+
 // Neighbour words of storage word sw of sublattice q, read from the other sublattice
 // array O.  X is the x-neighbour that is not at the same k (k-1 for p = 0, k+1 for
 // p = 1; the other x-neighbour is C itself), Ym/Yp/Zm/Zp are the rows y-1, y+1,

@@ -52,44 +52,6 @@ __device__ __forceinline__ uint4 xshift(const uint4 &C, uint32_t edge_left_w, ui
     return X;
 }
 
-__device__ __forceinline__ uint32_t maj3(uint32_t a, uint32_t b, uint32_t c) { return (a & b) | (c & (a ^ b)); }
-
-// New spins of the 128 sites of one uint4 (T -> 0 Glauber, Eq. 6).  With u the number of up
-// neighbours and tau the tie bit (the old spin for the rule that never flips at zero energy,
-// its complement for the rule that always flips, the old spin xor the random bit for Glauber),
-// the new spin is [u + tau >= 4]: up where u >= 4, tau where u = 3, down where u <= 2.  Two
-// full adders give u = s1 + s2 + 2 (c1 + c2); a third adds s1 + s2 + tau = s3 + 2 c3, so the
-// new spin is the majority of c1, c2, c3.  Glauber draws Philox only where some site of the
-// group has u = 3, i.e. s1 != s2 and c1 != c2.
-template <int RULE>
-__device__ __forceinline__ uint4 update4(const uint4 &s, const uint4 &C, const uint4 &X, const uint4 &ym,
-                                         const uint4 &yp, const uint4 &zm, const uint4 &zp, uint32_t group,
-                                         uint32_t t, uint32_t q, const PhiloxKeys &keys)
-{
-    const uint32_t s1x = C.x ^ X.x ^ ym.x, c1x = maj3(C.x, X.x, ym.x);
-    const uint32_t s1y = C.y ^ X.y ^ ym.y, c1y = maj3(C.y, X.y, ym.y);
-    const uint32_t s1z = C.z ^ X.z ^ ym.z, c1z = maj3(C.z, X.z, ym.z);
-    const uint32_t s1w = C.w ^ X.w ^ ym.w, c1w = maj3(C.w, X.w, ym.w);
-    const uint32_t s2x = yp.x ^ zm.x ^ zp.x, c2x = maj3(yp.x, zm.x, zp.x);
-    const uint32_t s2y = yp.y ^ zm.y ^ zp.y, c2y = maj3(yp.y, zm.y, zp.y);
-    const uint32_t s2z = yp.z ^ zm.z ^ zp.z, c2z = maj3(yp.z, zm.z, zp.z);
-    const uint32_t s2w = yp.w ^ zm.w ^ zp.w, c2w = maj3(yp.w, zm.w, zp.w);
-    uint4 tau;
-    if (RULE == TIE_GLAUBER) {
-        const uint32_t tie = ((s1x ^ s2x) & (c1x ^ c2x)) | ((s1y ^ s2y) & (c1y ^ c2y)) |
-                             ((s1z ^ s2z) & (c1z ^ c2z)) | ((s1w ^ s2w) & (c1w ^ c2w));
-        U4 o{0u, 0u, 0u, 0u};
-        if (tie != 0u) o = philox4x32_10_rk(group, t, q, 0u, keys);
-        tau = make_uint4(s.x ^ o.x, s.y ^ o.y, s.z ^ o.z, s.w ^ o.w);
-    } else if (RULE == TIE_ALWAYS) {
-        tau = make_uint4(~s.x, ~s.y, ~s.z, ~s.w);
-    } else {
-        tau = s;
-    }
-    return make_uint4(maj3(c1x, c2x, maj3(s1x, s2x, tau.x)), maj3(c1y, c2y, maj3(s1y, s2y, tau.y)),
-                      maj3(c1z, c2z, maj3(s1z, s2z, tau.z)), maj3(c1w, c2w, maj3(s1w, s2w, tau.w)));
-}
-
 }  // namespace
 
 // Shared memory: NS copy slots, each one B plane (rows y0-2 .. y0+TY+1) and one old-A plane
@@ -218,7 +180,7 @@ __global__ void __launch_bounds__(256, 3) k_mcs_fused(const uint32_t *__restrict
         {
             const uint32_t e = __shfl_sync(FULL, p ? bc.x : bc.w, p ? srcr : srcl, W4);
             const uint4 X = xshift(bc, e, e, p);
-            a0 = update4<RULE>(Bsp[NB + rN], bc, X, Bs0[rB - W4], Bs0[rB + W4], bm, bp, (uint32_t)oA, t,
+            a0 = new_spins4<RULE, false>(Bsp[NB + rN], bc, X, Bs0[rB - W4], Bs0[rB + W4], bm, bp, (uint32_t)oA, t,
                                (uint32_t)A, keys);
             An[rN] = a0;
             if (k >= 1 && k <= TZ) Anxt[oA] = a0;
@@ -230,7 +192,7 @@ __global__ void __launch_bounds__(256, 3) k_mcs_fused(const uint32_t *__restrict
             const int ph = p ^ 1 ^ hr;
             const uint32_t e = __shfl_sync(HMASK, ph ? hbc.x : hbc.w, ph ? srcr : srcl, W4);
             const uint4 X = xshift(hbc, e, e, ph);
-            An[hN] = update4<RULE>(Bsp[NB + hN], hbc, X, Bs0[hB - W4], Bs0[hB + W4], Bsm[hB], Bsp[hB],
+            An[hN] = new_spins4<RULE, false>(Bsp[NB + hN], hbc, X, Bs0[hB - W4], Bs0[hB + W4], Bsm[hB], Bsp[hB],
                                    (uint32_t)(oA + dh), t, (uint32_t)A, keys);
         }
         // B on plane zB = zA - 1, own column: new A of planes zB - 1, zB, zB + 1 are a2, a1, a0
@@ -238,7 +200,7 @@ __global__ void __launch_bounds__(256, 3) k_mcs_fused(const uint32_t *__restrict
             const uint4 *Ap = anew + ((k - 1) & 1) * RA * W4;  // new A, plane zB
             const uint32_t e = __shfl_sync(FULL, p ? a1.x : a1.w, p ? srcr : srcl, W4);
             const uint4 X = xshift(a1, e, e, p);
-            Bnxt[oB] = update4<RULE>(bm, a1, X, Ap[rN - W4], Ap[rN + W4], a2, a0, (uint32_t)oB, t, (uint32_t)B, keys);
+            Bnxt[oB] = new_spins4<RULE, false>(bm, a1, X, Ap[rN - W4], Ap[rN + W4], a2, a0, (uint32_t)oB, t, (uint32_t)B, keys);
         }
         a2 = a1;
         a1 = a0;
@@ -364,7 +326,7 @@ __global__ void __launch_bounds__(256, MINB)
         const uint4 bp = Bsp[rB];
         const uint32_t e = __shfl_sync(FULL, p ? bc.x : bc.w, p ? srcr : srcl, W4);
         const uint4 X = xshift(bc, e, e, p);
-        const uint4 a0 = update4<RULE>(Bsp[rA], bc, X, Bs0[rB - W4], Bs0[rB + W4], bm, bp, (uint32_t)(oz + own), t,
+        const uint4 a0 = new_spins4<RULE, false>(Bsp[rA], bc, X, Bs0[rB - W4], Bs0[rB + W4], bm, bp, (uint32_t)(oz + own), t,
                                        (uint32_t)A, keys);
         An[rN] = a0;
         if (bown && k >= 1 && k <= TZ) Anxt[oz + own] = a0;
@@ -373,7 +335,7 @@ __global__ void __launch_bounds__(256, MINB)
             const uint4 *Ap = anew + ((k - 1) & 1) * NT;  // new A, plane zB
             const uint32_t eb = __shfl_sync(FULL, p ? a1.x : a1.w, p ? srcr : srcl, W4);
             const uint4 Xb = xshift(a1, eb, eb, p);
-            const uint4 nb = update4<RULE>(bm, a1, Xb, Ap[rNm], Ap[rNp], a2, a0, (uint32_t)(ozB + own), t,
+            const uint4 nb = new_spins4<RULE, false>(bm, a1, Xb, Ap[rNm], Ap[rNp], a2, a0, (uint32_t)(ozB + own), t,
                                            (uint32_t)B, keys);
             if (bown) Bnxt[ozB + own] = nb;
         }

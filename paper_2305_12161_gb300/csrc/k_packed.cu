@@ -310,19 +310,7 @@ __global__ void __launch_bounds__(256) k_sweep_zfast(uint32_t *lat, Geom g, int 
             X.z = __funnelshift_r(cc.z, cc.w, 1);
             X.w = __funnelshift_r(cc.w, e, 1);
         }
-        uint32_t g0, g1, g2, g3, e0, e1, e2, e3;
-        count6(cc.x, X.x, ym.x, yp.x, cm.x, cp.x, g0, e0);
-        count6(cc.y, X.y, ym.y, yp.y, cm.y, cp.y, g1, e1);
-        count6(cc.z, X.z, ym.z, yp.z, cm.z, cp.z, g2, e2);
-        count6(cc.w, X.w, ym.w, yp.w, cm.w, cp.w, g3, e3);
-        U4 o{0u, 0u, 0u, 0u};
-        if (RULE == TIE_GLAUBER && (e0 | e1 | e2 | e3) != 0u) o = philox4x32_10_rk(gidx, t, (uint32_t)q, 0u, keys);
-        uint4 nw;
-        nw.x = resolve<RULE>(s.x, g0, e0, o.x);
-        nw.y = resolve<RULE>(s.y, g1, e1, o.y);
-        nw.z = resolve<RULE>(s.z, g2, e2, o.z);
-        nw.w = resolve<RULE>(s.w, g3, e3, o.w);
-        *sp = nw;
+        *sp = new_spins4<RULE>(s, cc, X, ym, yp, cm, cp, gidx, t, (uint32_t)q, keys);
         sp += plane4;
         gidx += gstep;
         p ^= 1;
