@@ -208,6 +208,27 @@ int ising_create_ex(ising_ctx **out, int L, int R, uint64_t seed, const ising_op
     if (o.scheme == ISING_SCHEME_DOUBLE &&
         (o.form != ISING_FORM_PACKED || !make_dcb_geom(L, o.block_x, o.block_y, o.block_z, &dcb)))
         return ISING_EINVAL;
+    // sweep kernel selection (host arithmetic only: a bad configuration is refused before
+    // the device is touched)
+    SweepConfig cfg{};
+    if (o.variant == 0) {
+        cfg = default_sweep_config(L, R);
+    } else {
+        cfg = SweepConfig{o.variant, o.tile_y, o.tile_z, o.variant == VARIANT_ZFUSE ? o.depth : (o.depth ? o.depth : 3)};
+        if ((cfg.variant == VARIANT_ZMARCH || cfg.variant == VARIANT_ZFAST || cfg.variant == VARIANT_ZDEEP ||
+             cfg.variant == VARIANT_ZFUSE) &&
+            (o.tile_y == 0 || o.tile_z == 0)) {
+            if (L >= 256 && L % 256 == 0) {
+                const int W4 = L / 256;
+                if (!cfg.tile_y) cfg.tile_y = std::max(1, 256 / W4);
+                if (!cfg.tile_z) cfg.tile_z = std::min(L, 16);
+            }
+        }
+        if ((cfg.variant == VARIANT_ZFAST || cfg.variant == VARIANT_ZDEEP || cfg.variant == VARIANT_ZFUSE) &&
+            L >= 256 && L % 256 == 0)
+            cfg.tile_y = 256 / (L / 256);
+        if (!sweep_config_valid(L, cfg)) return ISING_EINVAL;
+    }
     ising_ctx *c = new (std::nothrow) ising_ctx();
     if (!c) return ISING_ENOMEM;
     c->L = L;
@@ -216,6 +237,7 @@ int ising_create_ex(ising_ctx **out, int L, int R, uint64_t seed, const ising_op
     c->opts = o;
     c->g = make_geom(L);
     c->dcb = dcb;
+    c->cfg = cfg;
     int dev = o.device;
     if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) {
         delete c;
@@ -232,26 +254,6 @@ int ising_create_ex(ising_ctx **out, int L, int R, uint64_t seed, const ising_op
     } else {
         if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) return bail(ISING_ECUDA);
         c->own_stream = true;
-    }
-    // sweep kernel selection
-    if (o.variant == 0) {
-        c->cfg = default_sweep_config(L, R);
-    } else {
-        c->cfg = SweepConfig{o.variant, o.tile_y, o.tile_z,
-                             o.variant == VARIANT_ZFUSE ? o.depth : (o.depth ? o.depth : 3)};
-        if ((c->cfg.variant == VARIANT_ZMARCH || c->cfg.variant == VARIANT_ZFAST || c->cfg.variant == VARIANT_ZDEEP ||
-             c->cfg.variant == VARIANT_ZFUSE) &&
-            (o.tile_y == 0 || o.tile_z == 0)) {
-            if (L >= 256 && L % 256 == 0) {
-                const int W4 = L / 256;
-                if (!c->cfg.tile_y) c->cfg.tile_y = std::max(1, 256 / W4);
-                if (!c->cfg.tile_z) c->cfg.tile_z = std::min(L, 16);
-            }
-        }
-        if ((c->cfg.variant == VARIANT_ZFAST || c->cfg.variant == VARIANT_ZDEEP || c->cfg.variant == VARIANT_ZFUSE) &&
-            L >= 256 && L % 256 == 0)
-            c->cfg.tile_y = 256 / (L / 256);
-        if (!sweep_config_valid(L, c->cfg)) return bail(ISING_EINVAL);
     }
     // stream-ordered allocations (no implicit device synchronisation)
     const size_t pbytes = lattice_bytes_packed(L, R);

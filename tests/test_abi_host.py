@@ -64,6 +64,34 @@ def test_create_rejects_bad_arguments_before_touching_a_device(lib):
         assert lib.ising_create(ctypes.byref(h), L, R, 1) == ising.ISING_EINVAL
         assert h.value is None
     assert lib.ising_create(None, 64, 1, 1) == ising.ISING_EINVAL
+    # sweep-kernel configurations no kernel can run
+    bad = (dict(L=64, variant=9), dict(L=128, variant=ising.VARIANT_ZFUSE), dict(L=2048, variant=ising.VARIANT_ZFUSE,
+           depth=7), dict(L=2048, variant=ising.VARIANT_ZFUSE, tile_z=3), dict(L=2048, variant=ising.VARIANT_ZFAST,
+           tile_z=48), dict(L=1024, variant=ising.VARIANT_ZDEEP, depth=5), dict(L=96 * 4, variant=ising.VARIANT_ZFAST))
+    for kw in bad:
+        o = ising.ising_opts()
+        lib.ising_default_opts(ctypes.byref(o))
+        L = kw.pop("L")
+        for k, v in kw.items():
+            setattr(o, k, v)
+        assert lib.ising_create_ex(ctypes.byref(h), L, 1, 1, ctypes.byref(o)) == ising.ISING_EINVAL, (L, kw)
+        assert h.value is None
+    # valid ones pass the checks: without a device the call then fails on the device (with one
+    # it succeeds)
+    good = (dict(L=64), dict(L=256, variant=ising.VARIANT_ZFAST, tile_z=8), dict(L=2048, variant=ising.VARIANT_ZFUSE,
+            tile_z=32, depth=3), dict(L=1024, variant=ising.VARIANT_ZFUSE, tile_z=32, depth=10),
+            dict(L=512, variant=ising.VARIANT_ZDEEP, tile_z=16, depth=4))
+    for kw in good:
+        o = ising.ising_opts()
+        lib.ising_default_opts(ctypes.byref(o))
+        L = kw.pop("L")
+        for k, v in kw.items():
+            setattr(o, k, v)
+        st = lib.ising_create_ex(ctypes.byref(h), L, 1, 1, ctypes.byref(o))
+        assert st in (ising.ISING_OK, ising.ISING_ECUDA), (L, kw, st)
+        if st == ising.ISING_OK:
+            lib.ising_destroy(h)
+        h = ctypes.c_void_p()
     # NULL-safe destroy and NULL-context calls
     assert lib.ising_destroy(None) == ising.ISING_OK
     assert lib.ising_sweep(None, 1) == ising.ISING_EINVAL
