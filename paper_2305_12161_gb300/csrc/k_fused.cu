@@ -13,7 +13,9 @@
 // storage group), so the trajectory is bit-identical to two half-sweep launches.
 //
 // Per sweep the store is read once (plus L2-served halo rows and planes) and written once:
-// N/4 bytes, against 3 N/8 for two half-sweeps.
+// N/4 bytes, against 3 N/8 for two half-sweeps.  Two tilings: k_mcs_fused (tiles of
+// 256 / W4 rows, the halo rows of A on extra lanes of warp 0) and k_mcs_fused_bal (256 / W4
+// computed rows of which the outer two are the halo, so every warp does the same work).
 #include "common.cuh"
 #include "kernels.h"
 
