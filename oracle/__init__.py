@@ -35,7 +35,7 @@ def build(force: bool = False) -> str:
     if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
         return _LIB
     cc = os.environ.get("CC", "gcc")
-    base = [cc, "-O2", "-std=c11", "-fPIC", "-shared", _SRC, "-o", _LIB + ".tmp", "-lm"]
+    base = [cc, "-O3", "-std=c11", "-fPIC", "-shared", _SRC, "-o", _LIB + ".tmp", "-lm"]
     try:
         subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
     except subprocess.CalledProcessError:
@@ -79,6 +79,8 @@ def lib() -> ctypes.CDLL:
             L.orc_magnetisation_bonds.restype = None
             L.orc_corr_lag.argtypes = [ctypes.c_int, i8p, ctypes.c_int64, i64p]
             L.orc_corr_lag.restype = None
+            L.orc_corr_lags.argtypes = [ctypes.c_int, i8p, i64p, ctypes.c_int64, i64p]
+            L.orc_corr_lags.restype = None
             L.orc_menger_member.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int]
             L.orc_menger_member.restype = ctypes.c_int
             L.orc_menger_tile_sign.argtypes = [ctypes.c_uint64, ctypes.c_int64]
@@ -306,6 +308,18 @@ def corr_lag(s: np.ndarray, r: int) -> np.ndarray:
     L = _check_lattice(s)
     out = np.zeros(3, dtype=np.int64)
     lib().orc_corr_lag(L, _p(s, ctypes.c_int8), r, _p(out, ctypes.c_int64))
+    return out
+
+
+def corr_lags(s: np.ndarray, lags) -> np.ndarray:
+    """[n, 3] array of [D_x(r), D_y(r), D_z(r)] for the lags r (each in [0, L)), counted
+    line by line (the counting ``record`` uses)."""
+    L = _check_lattice(s)
+    lg = np.ascontiguousarray(lags, dtype=np.int64)
+    if lg.ndim != 1 or (lg.size and (lg.min() < 0 or lg.max() >= L)):
+        raise ValueError("lags must be a 1-d list of values in [0, L)")
+    out = np.zeros((lg.size, 3), dtype=np.int64)
+    lib().orc_corr_lags(L, _p(s, ctypes.c_int8), _p(lg, ctypes.c_int64), lg.size, _p(out, ctypes.c_int64))
     return out
 
 

@@ -259,20 +259,66 @@ void orc_corr_lag(int L_, const int8_t *s, int64_t r, int64_t *D3)
     D3[2] = dz;
 }
 
+/* D_x(r), D_y(r), D_z(r) for the n distances lags[0..n), each in [0, L), written to
+ * D3[3j + a].  Same definition as orc_corr_lag, counted line by line: the L sites of one
+ * periodic line along axis a are copied twice in a row into a buffer, so that the
+ * partner of position k at distance r is buffer entry k + r, and every lag is one pass
+ * over the buffer.  A second, independent way of counting Eq. (2)'s pairs: the tests
+ * require it to equal orc_corr_lag at every lag on small lattices. */
+void orc_corr_lags(int L_, const int8_t *s, const int64_t *lags, int64_t n, int64_t *D3)
+{
+    const int64_t L = L_;
+    for (int64_t k = 0; k < 3 * n; ++k) D3[k] = 0;
+    for (int a = 0; a < 3; ++a) {
+        /* step along the line, and the steps of the two coordinates that fix the line
+         * (the faster one first, so that consecutive lines share cache lines) */
+        const int64_t sa = a == 0 ? 1 : (a == 1 ? L : L * L);
+        const int64_t su = a == 0 ? L : 1;
+        const int64_t sv = a == 2 ? L : L * L;
+#pragma omp parallel
+        {
+            int8_t *ln = (int8_t *)malloc((size_t)(2 * L));
+            int64_t *acc = (int64_t *)calloc((size_t)(n > 0 ? n : 1), sizeof(int64_t));
+#pragma omp for schedule(static)
+            for (int64_t line = 0; line < L * L; ++line) {
+                const int64_t base = (line % L) * su + (line / L) * sv;
+                for (int64_t k = 0; k < L; ++k) {
+                    ln[k] = s[base + k * sa];
+                    ln[L + k] = ln[k];
+                }
+                for (int64_t j = 0; j < n; ++j) {
+                    const int8_t *p = ln + lags[j];
+                    int32_t c = 0;
+                    for (int64_t k = 0; k < L; ++k) c += (ln[k] != p[k]);
+                    acc[j] += c;
+                }
+            }
+#pragma omp critical
+            for (int64_t j = 0; j < n; ++j) D3[3 * j + a] += acc[j];
+            free(ln);
+            free(acc);
+        }
+    }
+}
+
 void orc_record(int L_, const int8_t *s, int64_t t, int64_t *rec)
 {
     const int64_t L = L_;
     const int64_t R = L / 2;
     rec[0] = t;
     orc_magnetisation_bonds(L_, s, &rec[1], &rec[2]);
+    int64_t *lags = (int64_t *)malloc(sizeof(int64_t) * (size_t)(R + 1));
+    int64_t *D3 = (int64_t *)malloc(sizeof(int64_t) * 3 * (size_t)(R + 1));
+    for (int64_t r = 0; r <= R; ++r) lags[r] = r;
+    orc_corr_lags(L_, s, lags, R + 1, D3);
     int64_t *Dx = rec + 3, *Dy = rec + 3 + (R + 1), *Dz = rec + 3 + 2 * (R + 1);
     for (int64_t r = 0; r <= R; ++r) {
-        int64_t D3[3];
-        orc_corr_lag(L_, s, r, D3);
-        Dx[r] = D3[0];
-        Dy[r] = D3[1];
-        Dz[r] = D3[2];
+        Dx[r] = D3[3 * r + 0];
+        Dy[r] = D3[3 * r + 1];
+        Dz[r] = D3[3 * r + 2];
     }
+    free(D3);
+    free(lags);
 }
 
 /* ------------------------------------------------------------------------------ */

@@ -145,3 +145,34 @@ def test_run_records_schedule():
     assert list(recs[:, 0]) == [0, 1, 2, 5]
     # B never rises along a quench
     assert all(b >= a for a, b in zip(recs[1:, 2], recs[:-1, 2]))
+
+
+@pytest.mark.parametrize("L,seed", [(4, 0), (6, 1), (16, 2), (34, 3)])
+def test_line_counting_equals_site_counting(L, seed):
+    # the record counts D_a(r) line by line (orc_corr_lags); orc_corr_lag counts the same
+    # pairs site by site with periodic wrapping.  Two independent loops over Eq. (2)'s pairs
+    # must agree at every distance, including those beyond L/2
+    s = inputs.random_state(L, seed, p_up=0.4)
+    rec = oracle.record(s)
+    D = _D(rec, L)
+    for r in range(L // 2 + 1):
+        assert list(D[:, r]) == list(oracle.corr_lag(s, r)), r
+    allD = oracle.corr_lags(s, list(range(L)))
+    for r in range(L):
+        assert list(allD[r]) == list(oracle.corr_lag(s, r)), r
+    # lags in any order and repeated
+    lags = [3, 0, L - 1, 3]
+    assert np.array_equal(oracle.corr_lags(s, lags), allD[lags])
+
+
+def test_line_counting_planted_structure():
+    # a single flipped site in a uniform state: every axis has exactly 2 unequal pairs at
+    # every distance r = 1..L-1, and 0 at r = 0 -- checks that each line is counted once
+    L = 12
+    s = inputs.uniform_state(L)
+    s[5, 7, 3] = -1
+    D = oracle.corr_lags(s, list(range(L)))
+    assert np.all(D[0] == 0)
+    assert np.all(D[1:] == 2)
+    with pytest.raises(ValueError):
+        oracle.corr_lags(s, [L])
