@@ -149,7 +149,8 @@ def run_quench_case(args):
     if args.sweep_config:
         v, ty, tz, dp = (int(x) for x in args.sweep_config.split(","))
         kw = dict(variant=v, tile_y=ty, tile_z=tz, depth=dp)
-    with ising.Ising(args.L, replicas=1, seed=1, corr=args.corr, **kw) as q:
+    form = ising.FORM_PLAIN if args.form == "plain" else ising.FORM_PACKED
+    with ising.Ising(args.L, replicas=1, seed=1, corr=args.corr, form=form, **kw) as q:
         q.sweep(args.mcs)
         rec, der = q.measure_ex(c=0.5)
         print(json.dumps({"case": "quench", "L": args.L, "mcs": args.mcs, "B": int(rec[0, 2]),
@@ -157,6 +158,10 @@ def run_quench_case(args):
 
 
 BATCH_CLASSES = [(64, 512, 1), (128, 64, 513), (256, 16, 577), (512, 4, 593)]  # seeds 1..596
+
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of a sweep kernel, from
+# one ncu capture each (the file under profiles/ gives the command); (kernel, L) -> (bytes, source)
+TRAFFIC_NCU = {("k_sweep_zfast", 2048): (1.596e9, "ncu, profiles/k_sweep_zfast_L2048.md")}
 
 
 def run_batched(torch, ising, inputs, K: int = 20, window: int = 20) -> dict:
@@ -216,6 +221,56 @@ def run_batched(torch, ising, inputs, K: int = 20, window: int = 20) -> dict:
             c.destroy()
     out["batched_vs_plain"] = out["batched_window_updates_per_ns"] / out["plain_window_updates_per_ns"]
     return out
+
+
+def run_plain(torch, ising, pk, sizes=(1024, 2048), mcs: int = 10, warm: int = 2) -> dict:
+    """The plain form at one lattice: one byte per spin, one kernel launch per half-sweep
+    (k_sweep_plain), T = infinity start, `warm` untimed MCS then `mcs` timed MCS (CUDA
+    events on the context's stream).  Algorithmic bytes: a half-sweep reads the whole
+    L^3-byte lattice (the sites of both sublattices share every 32-byte sector) and writes
+    back every sector that holds a site of the updated sublattice (L^3 bytes): 2 L^3 bytes
+    per L^3/2 updates = 4 B/update.  Both lattices are larger than L2."""
+    out = {}
+    for L in sizes:
+        stream = torch.cuda.Stream()
+        with ising.Ising(L, replicas=1, seed=1, form=ising.FORM_PLAIN, stream=stream) as q:
+            q.sweep(warm)
+            q.sync()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            q.sweep(mcs)
+            b.record(stream)
+            q.sync()
+            ms = a.elapsed_time(b)
+        N = L**3
+        half_s = ms * 1e-3 / (2 * mcs)
+        gbs = 2 * N / half_s / 1e9
+        out[str(L)] = {"updates_per_ns": N * mcs / (ms * 1e-3) / 1e9, "ms_per_mcs": ms / mcs,
+                       "avg_launch_ms": half_s * 1e3, "bytes_per_launch": 2 * N, "achieved_gbs": gbs,
+                       "peak_gbs": pk["hbm_gbs"], "frac": gbs / pk["hbm_gbs"], "mcs_timed": mcs,
+                       "t_window": [warm, warm + mcs]}
+        torch.cuda.empty_cache()
+    return out
+
+
+def run_serving(serve, requests: int = 16) -> dict:
+    """Continuous-batching serving on the first `requests` arrivals of the seeded trace
+    (Poisson 20/s, L log-uniform on {64..1024}, t_max = 10^U[3,5], 1-16 replicas, 12
+    measured times each), 150 GB budget by library footprint, 16 slots."""
+    trace = serve.trace_requests(requests, seed=0, K=12)
+    offered = sum(r.L**3 * r.replicas * r.t_max for r in trace)
+    srv = serve.QuenchServer(budget_bytes=150e9, max_slots=16, quantum_mcs=64)
+    srv.run(trace)
+    summ = srv.summary()
+    arrivals = trace[-1].arrival_s
+    return {"requests": summ["requests"], "p50_s": summ["p50_s"], "p99_s": summ["p99_s"],
+            "makespan_s": summ["makespan_s"], "aggregate_updates_per_ns": summ["updates_per_ns"],
+            "updates": summ["updates"],
+            "offered_updates_per_s": offered / arrivals if arrivals > 0 else None,
+            "trace": f"first {requests} arrivals: seeded Poisson 20/s, L log-uniform {{64,...,1024}}, "
+                     "t_max=10^U[3,5], replicas U{1..16}, K=12; overloaded (offered >> capacity)",
+            "slots": 16, "budget_gb": 150, "quantum_mcs": 64}
 
 
 def aggregate_ranks(ms: float, updates: float, dist=None, device=None) -> tuple[float, float]:
@@ -427,6 +482,10 @@ def main():
                     help="quench: init + --mcs sweeps + one measurement, untimed (for profilers); "
                          "serve: the serving loop on the first --requests arrivals of the seeded trace")
     ap.add_argument("--requests", type=int, default=24)
+    ap.add_argument("--serve-requests", type=int, default=16, help="serving leg of the default run: first arrivals")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--form", default="packed", choices=["packed", "plain"], help="quench case: lattice form")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -579,6 +638,14 @@ def main():
     batched = None
     if not args.no_batched and rank == 0:
         batched = run_batched(torch, ising, inputs)
+    pk = _peaks()
+    plain = None
+    if not args.no_plain and rank == 0:
+        plain = run_plain(torch, ising, pk)
+    serving = None
+    if not args.no_serve and rank == 0:
+        from paper_2305_12161_gb300 import serve
+        serving = run_serving(serve, args.serve_requests)
 
     updates_per_step = 2 * MCS * N
     _, job_updates = aggregate_ranks(ms, float(updates_per_step * args.steps), dist, "cuda")
@@ -590,7 +657,6 @@ def main():
     leg_ms = [sum(a.elapsed_time(b) for a, b, _, lg in sweep_events if lg == g) for g in (0, 1)]
     leg_launches = [sum(n for _, _, n, lg in sweep_events if lg == g) for g in (0, 1)]
     meas_ms = sum(a.elapsed_time(b) for a, b in meas_events)
-    pk = _peaks()
     fused = tuned["variant"] == 5
     # a half-sweep reads q and q-bar and writes q (1 bit per site each: 3 N/16 bytes); the fused
     # sweep reads both sublattices and writes both (N/4 bytes) and updates all N sites
@@ -611,16 +677,19 @@ def main():
     p_pop, a_pop, p_csa, a_csa = 1.0, 1.0, 1.0 / 8, 22.0 / 8
     f_pop = (a_csa / 64 - p_csa / 16) / ((p_pop - p_csa) / 16 + (a_csa - a_pop) / 64)
     words_per_clk = 16 / (f_pop * p_pop + (1 - f_pop) * p_csa)
-    popc_peak = 152 * words_per_clk * pk["sm_max_mhz"] * 1e6 / 1e12  # T word pairs/s
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    popc_peak = sms * words_per_clk * pk["sm_max_mhz"] * 1e6 / 1e12  # T word pairs/s
     corr_tops = corr_ops / meas_avg_s / 1e12
     kname = {1: "k_sweep_word", 2: "k_sweep_zmarch", 3: "k_sweep_zfast", 4: "k_sweep_zdeep",
              5: "k_mcs_fused"}[tuned["variant"]]
-    # DRAM bytes per launch from one ncu capture of the same kernel at L=2048 (sweep t=2);
-    # only quoted for the kernel that capture measured (k_sweep_zfast, 32-plane tiles)
-    traffic = {3: 1.596e9}.get(tuned["variant"]) if L == 2048 else None
+    # DRAM bytes per launch are not measured here (that needs a profiler): they are quoted
+    # from the ncu capture of the same kernel at L=2048 named in traffic_src, and only for
+    # the kernel that capture measured
+    traffic, traffic_src = TRAFFIC_NCU.get((kname, L), (None, None))
     roof_sweep = {"kernel": kname + (" (whole sweep)" if fused else " (half-sweep)"), "bound": "hbm",
                   "achieved": sweep_gbs,
                   "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": sweep_gbs / pk["hbm_gbs"], "traffic": traffic,
+                  "traffic_src": traffic_src,
                   "peak_src": pk["src"], "avg_launch_ms": sweep_avg_s * 1e3, "bytes_per_launch": bytes_per_launch,
                   "updates_per_ns": sites_per_launch / sweep_avg_s / 1e9}
     if tensor_corr:
@@ -666,6 +735,7 @@ def main():
             "sweep_config": tuned,
             "corr_method": "tensor cores (tcgen05 Gram)" if tensor_corr else "bit counts",
             "clocks": clk, "e2e": e2e, "gpu_launches": launches, "batched": batched,
+            "plain": plain, "serving": serving,
             "cpu_baseline": cpu,
         }
         print(json.dumps(out))

@@ -143,6 +143,19 @@ void ising_default_opts(ising_opts *opts);
 int ising_create(ising_ctx **out, int L, int replicas, uint64_t seed);
 int ising_create_ex(ising_ctx **out, int L, int replicas, uint64_t seed, const ising_opts *opts);
 
+/* Device bytes that a context of `replicas` lattices of size L with options *opts (NULL:
+ * defaults) holds once it has measured: the packed store (2 x L^3/16 bytes per replica,
+ * twice for the fused whole-sweep kernel, variant 5), the byte-per-spin lattice of the
+ * PLAIN form (L^3 per replica), the records and derived values, and the tensor-core
+ * correlation scratch (L^3 bytes, allocated by the first measurement whose method is the
+ * tensor-core path: ISING_CORR_TENSOR, or AUTO with L >= 512).  Pure host arithmetic,
+ * no device is touched; what ising_create_ex allocates comes from the same accounting.
+ * Not included: buffers that only the optional calls allocate while they run or keep
+ * (get/set_spins stage L^3 bytes for the duration of the call; ising_measure_radial keeps
+ * its FFT buffer and ISING_PTR_HOST_ASYNC its staging copy until ising_release_scratch).
+ * Returns -1 for arguments that ising_create_ex would refuse. */
+int64_t ising_footprint_bytes(int L, int replicas, const ising_opts *opts);
+
 /* Redraw every replica's T = infinity initial state for a new seed (replica r uses
  * seed + r) and reset t to 0, reusing the context's memory.  Enqueued, no sync. */
 int ising_reinit(ising_ctx *ctx, uint64_t seed);
@@ -341,7 +354,7 @@ int ising_batch_destroy(ising_batch *b);
  * This entry point allocates nothing: the caller passes the packed lattices (device
  * memory, `replicas` consecutive states in the ising_get_packed layout) and a device
  * output `derived` of replicas x 4 doubles [e, m, l_E, l_C] (as in ising_measure_ex,
- * with the same flags except ISING_MEAS_DEVICE, which is implied).  The integer
+ * with the same flags; ISING_MEAS_DEVICE is implied, accepted and ignored).  The integer
  * records it builds on the way live in one fixed array inside the library's device
  * image, ISING_NOALLOC_MAX_RECORD_WORDS int64 (1 MiB), which every GPU that loads the
  * library holds until the process exits.

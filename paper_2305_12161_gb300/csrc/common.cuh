@@ -3,10 +3,26 @@
 // the bit-sliced six-neighbour majority of the T -> 0 Glauber rule.
 #pragma once
 
+#include <atomic>
 #include <cstdint>
 #include <cuda_runtime.h>
 
 namespace ising {
+
+// Streaming multiprocessors of the current device (looked up once per device), for grid
+// caps and tile heuristics.  1 if the query fails: every kernel sized by it strides over
+// its work, so a small grid is slower, never wrong.
+inline int device_sms()
+{
+    static std::atomic<int> cache[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+    int v = cache[dev].load(std::memory_order_relaxed);
+    if (v > 0) return v;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) return 1;
+    cache[dev].store(v, std::memory_order_relaxed);
+    return v;
+}
 
 enum Rule : int { TIE_GLAUBER = 0, TIE_ALWAYS = 1, TIE_NEVER = 2 };
 

@@ -188,13 +188,14 @@ int ising_destroy(ising_ctx *c)
     return ISING_OK;
 }
 
-int ising_create_ex(ising_ctx **out, int L, int R, uint64_t seed, const ising_opts *opts)
+}  // extern "C"
+
+namespace {
+
+// Argument checks of a context and its sweep kernel choice (host arithmetic only: a bad
+// configuration is refused before the device is touched).
+int resolve_opts(int L, int R, const ising_opts &o, SweepConfig *cfg_out, DcbGeom *dcb_out)
 {
-    if (!out) return ISING_EINVAL;
-    *out = nullptr;
-    ising_opts o;
-    ising_default_opts(&o);
-    if (opts) o = *opts;
     if (L < 4 || L % 2 != 0 || R < 1 || R > 65535) return ISING_EINVAL;
     if (o.tie < 0 || o.tie > 2 || (o.form != ISING_FORM_PACKED && o.form != ISING_FORM_PLAIN)) return ISING_EINVAL;
     if (o.cycle != ISING_CYCLE_01 && o.cycle != ISING_CYCLE_MIXED) return ISING_EINVAL;
@@ -208,8 +209,6 @@ int ising_create_ex(ising_ctx **out, int L, int R, uint64_t seed, const ising_op
     if (o.scheme == ISING_SCHEME_DOUBLE &&
         (o.form != ISING_FORM_PACKED || !make_dcb_geom(L, o.block_x, o.block_y, o.block_z, &dcb)))
         return ISING_EINVAL;
-    // sweep kernel selection (host arithmetic only: a bad configuration is refused before
-    // the device is touched)
     SweepConfig cfg{};
     if (o.variant == 0) {
         cfg = default_sweep_config(L, R);
@@ -229,6 +228,67 @@ int ising_create_ex(ising_ctx **out, int L, int R, uint64_t seed, const ising_op
             cfg.tile_y = 256 / (L / 256);
         if (!sweep_config_valid(L, cfg)) return ISING_EINVAL;
     }
+    if (cfg_out) *cfg_out = cfg;
+    if (dcb_out) *dcb_out = dcb;
+    return ISING_OK;
+}
+
+// Device memory of a context, by buffer.  ising_create_ex allocates exactly the first six
+// at creation; the correlation scratch is allocated by the first measurement that runs the
+// tensor-core path and then kept.
+struct Footprint {
+    size_t lat, lat_alt, plain, rec, der, err, corr;
+    size_t total() const { return lat + lat_alt + plain + rec + der + err + corr; }
+};
+
+// Whether a measurement of this context runs the tensor-core correlation (before any
+// allocation was refused).
+bool wants_tensor_corr(int L, const ising_opts &o)
+{
+    return o.corr == ISING_CORR_TENSOR || (o.corr == ISING_CORR_AUTO && L >= 512 && corr_mma_supported(L));
+}
+
+Footprint footprint_of(int L, int R, const ising_opts &o, const SweepConfig &cfg)
+{
+    Footprint f{};
+    f.lat = lattice_bytes_packed(L, R);
+    f.lat_alt = (cfg.variant == VARIANT_ZFUSE && o.form == ISING_FORM_PACKED && o.scheme == ISING_SCHEME_CHECKERBOARD)
+                    ? f.lat
+                    : 0;
+    f.plain = o.form == ISING_FORM_PLAIN ? (size_t)R * (size_t)L * L * L : 0;
+    f.rec = sizeof(int64_t) * (size_t)R * (size_t)ising_record_len(L);
+    f.der = sizeof(double) * 4 * (size_t)R;
+    f.err = sizeof(int) * 4;
+    f.corr = wants_tensor_corr(L, o) ? corr_mma_scratch_bytes(L, R) : 0;
+    return f;
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t ising_footprint_bytes(int L, int R, const ising_opts *opts)
+{
+    ising_opts o;
+    ising_default_opts(&o);
+    if (opts) o = *opts;
+    SweepConfig cfg{};
+    if (resolve_opts(L, R, o, &cfg, nullptr) != ISING_OK) return -1;
+    return (int64_t)footprint_of(L, R, o, cfg).total();
+}
+
+int ising_create_ex(ising_ctx **out, int L, int R, uint64_t seed, const ising_opts *opts)
+{
+    if (!out) return ISING_EINVAL;
+    *out = nullptr;
+    ising_opts o;
+    ising_default_opts(&o);
+    if (opts) o = *opts;
+    SweepConfig cfg{};
+    DcbGeom dcb{};
+    const int st = resolve_opts(L, R, o, &cfg, &dcb);
+    if (st != ISING_OK) return st;
+    const Footprint fp = footprint_of(L, R, o, cfg);
     ising_ctx *c = new (std::nothrow) ising_ctx();
     if (!c) return ISING_ENOMEM;
     c->L = L;
@@ -255,23 +315,17 @@ int ising_create_ex(ising_ctx **out, int L, int R, uint64_t seed, const ising_op
         if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) return bail(ISING_ECUDA);
         c->own_stream = true;
     }
-    // stream-ordered allocations (no implicit device synchronisation)
-    const size_t pbytes = lattice_bytes_packed(L, R);
-    if (cudaMallocAsync((void **)&c->lat, pbytes, c->stream) != cudaSuccess) return bail(ISING_ENOMEM);
-    if (c->cfg.variant == VARIANT_ZFUSE && o.form == ISING_FORM_PACKED && o.scheme == ISING_SCHEME_CHECKERBOARD &&
-        cudaMallocAsync((void **)&c->lat_alt, pbytes, c->stream) != cudaSuccess)
+    // stream-ordered allocations (no implicit device synchronisation); sizes from the same
+    // accounting that ising_footprint_bytes reports
+    const size_t pbytes = fp.lat;
+    if (cudaMallocAsync((void **)&c->lat, fp.lat, c->stream) != cudaSuccess) return bail(ISING_ENOMEM);
+    if (fp.lat_alt && cudaMallocAsync((void **)&c->lat_alt, fp.lat_alt, c->stream) != cudaSuccess)
         return bail(ISING_ENOMEM);
-    if (o.form == ISING_FORM_PLAIN) {
-        const size_t nbytes = (size_t)R * (size_t)L * L * L;
-        if (cudaMallocAsync((void **)&c->plain, nbytes, c->stream) != cudaSuccess) return bail(ISING_ENOMEM);
-    }
-    if (cudaMallocAsync((void **)&c->rec_dev, sizeof(int64_t) * (size_t)R * ising_record_len(L), c->stream) !=
-        cudaSuccess)
-        return bail(ISING_ENOMEM);
-    if (cudaMallocAsync((void **)&c->der_dev, sizeof(double) * 4 * (size_t)R, c->stream) != cudaSuccess)
-        return bail(ISING_ENOMEM);
-    if (cudaMallocAsync((void **)&c->dev_err, sizeof(int) * 4, c->stream) != cudaSuccess) return bail(ISING_ENOMEM);
-    if (cudaMemsetAsync(c->dev_err, 0, sizeof(int) * 4, c->stream) != cudaSuccess) return bail(ISING_ECUDA);
+    if (fp.plain && cudaMallocAsync((void **)&c->plain, fp.plain, c->stream) != cudaSuccess) return bail(ISING_ENOMEM);
+    if (cudaMallocAsync((void **)&c->rec_dev, fp.rec, c->stream) != cudaSuccess) return bail(ISING_ENOMEM);
+    if (cudaMallocAsync((void **)&c->der_dev, fp.der, c->stream) != cudaSuccess) return bail(ISING_ENOMEM);
+    if (cudaMallocAsync((void **)&c->dev_err, fp.err, c->stream) != cudaSuccess) return bail(ISING_ENOMEM);
+    if (cudaMemsetAsync(c->dev_err, 0, fp.err, c->stream) != cudaSuccess) return bail(ISING_ECUDA);
     cudaError_t e;
     if (o.form == ISING_FORM_PLAIN) {
         e = launch_init_plain(c->plain, L, R, seed, c->stream);
@@ -464,8 +518,7 @@ int ising_measure_ex(ising_ctx *c, int64_t *rec, double *derived, double cval, u
     int method = CORR_NONE;
     if (corr) {
         method = CORR_POPCOUNT;
-        if (c->opts.corr == ISING_CORR_TENSOR ||
-            (c->opts.corr == ISING_CORR_AUTO && c->L >= 512 && corr_mma_supported(c->L) && !c->xt_refused))
+        if (wants_tensor_corr(c->L, c->opts) && !(c->opts.corr == ISING_CORR_AUTO && c->xt_refused))
             method = CORR_TENSOR;
     }
     if (method == CORR_TENSOR && !c->xt) {

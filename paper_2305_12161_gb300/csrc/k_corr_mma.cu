@@ -218,8 +218,19 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *tm,
 // stage by tcgen05.commit; then all four warps read the accumulator and add each entry of an
 // upper-triangle tile (bk >= bj, bk < nb) as -G/2 to D at its cyclic distance.  The CTAs of
 // one K slice run together and stream the same columns, so L2 serves the tiles' repeated
-// reads.  Every wait is bounded; one that gives up sets *err and the CTA stops after releasing
-// its tensor memory.
+// reads.
+//
+// Every wait is bounded (timeout_ns of %globaltimer).  A wait that gives up clears the CTA's
+// `flag`, sets *err and the CTA stops without adding anything to D.  Before it leaves:
+//  * the producer waits, bounded, on the `full` barrier of every stage whose TMA loads it
+//    issued and the MMA thread did not consume, so that no bulk copy is still writing this
+//    CTA's shared memory when the CTA exits (stages [mma_end, prod_end) of the ring);
+//  * the MMA thread commits every MMA it issued to `done` and waits for it; only when that
+//    commit has arrived is the tensor memory released.  If it has not (no MMA on resident
+//    operands takes seconds, so this is not expected), the CTA records *err = 2 and skips
+//    the dealloc rather than free tensor memory the tensor core may still write.
+// No test provokes these paths; the stall test drops stage 0's loads of CTA 0 before any
+// load or MMA is in flight.
 __global__ void __launch_bounds__(128, 1) k_gram_tma(const __grid_constant__ CUtensorMap tmA,
                                                      const __grid_constant__ CUtensorMap tmB, int L, int nb,
                                                      int nunits, int split, int64_t *D, int *err,
@@ -233,6 +244,8 @@ __global__ void __launch_bounds__(128, 1) k_gram_tma(const __grid_constant__ CUt
     uint64_t *done = empty + GT_STAGES;
     uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(done + 1);
     int *flag = reinterpret_cast<int *>(tmem_holder + 1);
+    int *mma_end = flag + 1;      // stages whose operands the MMA thread waited for
+    int *mma_pending = flag + 2;  // 1: issued MMAs not known to be complete (keep the TMEM)
 
     const int H = L / 2;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -264,12 +277,15 @@ __global__ void __launch_bounds__(128, 1) k_gram_tma(const __grid_constant__ CUt
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(done)));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         *flag = 1;
+        *mma_end = 0;
+        *mma_pending = 0;
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_holder;
 
+    int prod_end = 0;  // producer: stages [0, prod_end) were armed (expect_tx) and loaded
     if (tid == 0) {  // producer
         for (int t = 0; t < n; ++t) {
             const int st = t % GT_STAGES;
@@ -281,6 +297,7 @@ __global__ void __launch_bounds__(128, 1) k_gram_tma(const __grid_constant__ CUt
             if (!*(volatile int *)flag) break;
             const uint32_t sa = smem_u32(stage0 + st * GT_STAGE_BYTES);
             mbar_expect_tx(smem_u32(&full[st]), GT_STAGE_BYTES);
+            prod_end = t + 1;
             if (inject && blockIdx.x == 0 && t == 0) continue;  // test hook: this stage never fills
             tma_load_2d(sa, &tmA, 0, (c0 + t) * L + j0, smem_u32(&full[st]));
             tma_load_2d(sa + TM_T * GT_KB, &tmB, 0, (c0 + t) * L + s0, smem_u32(&full[st]));
@@ -289,6 +306,7 @@ __global__ void __launch_bounds__(128, 1) k_gram_tma(const __grid_constant__ CUt
         int t = 0;
         for (; t < n; ++t) {
             const int st = t % GT_STAGES;
+            if (!*(volatile int *)flag) break;
             if (!mbar_wait(smem_u32(&full[st]), (uint32_t)((t / GT_STAGES) & 1), timeout_ns)) {
                 *flag = 0;
                 break;
@@ -306,10 +324,25 @@ __global__ void __launch_bounds__(128, 1) k_gram_tma(const __grid_constant__ CUt
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                 smem_u32(&empty[st])));
         }
+        *mma_end = t;
         if (t > 0) {  // the last commit covers every MMA before it
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                 smem_u32(done)));
-            if (!mbar_wait(smem_u32(done), 0u, timeout_ns)) *flag = 0;
+            if (!mbar_wait(smem_u32(done), 0u, timeout_ns)) {
+                *flag = 0;
+                // one more bounded window before the tensor memory is declared still in use
+                if (!mbar_wait(smem_u32(done), 0u, timeout_ns)) *mma_pending = 1;
+            }
+        }
+    }
+    __syncthreads();
+    if (tid == 0 && !*flag) {
+        // drain: every stage armed and loaded but not consumed by the MMA thread lands
+        // before the CTA may leave (at most GT_STAGES of them, all distinct ring slots)
+        for (int t = *mma_end; t < prod_end; ++t) {
+            if (inject && blockIdx.x == 0 && t == 0) continue;  // no load was issued for it
+            if (!mbar_wait(smem_u32(&full[t % GT_STAGES]), (uint32_t)((t / GT_STAGES) & 1), timeout_ns))
+                atomicExch(err, 3);
         }
     }
     __syncthreads();
@@ -345,16 +378,18 @@ __global__ void __launch_bounds__(128, 1) k_gram_tma(const __grid_constant__ CUt
             }
         }
     }
-    if (!*flag && tid == 0) atomicExch(err, 1);
+    if (!*flag && tid == 0) atomicCAS(err, 0, 1);
+    if (*mma_pending && tid == 0) atomicExch(err, 2);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(GT_N));
+    if (warp == 0 && !*mma_pending)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(GT_N));
     if (!ok) return;
     for (int i = 1 + tid; i <= H; i += 128)
         if (sacc[i]) atomicAdd((unsigned long long *)(D + i), (unsigned long long)(-(sacc[i] / 2)));
 }
 
-static size_t gram_smem_bytes() { return (size_t)GT_STAGES * GT_STAGE_BYTES + 1026 * 8 + (2 * GT_STAGES + 1) * 8 + 16; }
+static size_t gram_smem_bytes() { return (size_t)GT_STAGES * GT_STAGE_BYTES + 1026 * 8 + (2 * GT_STAGES + 1) * 8 + 32; }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,

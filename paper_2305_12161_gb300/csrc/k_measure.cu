@@ -409,11 +409,11 @@ cudaError_t launch_measure(const uint32_t *lat, int L, int R, int64_t t, int cor
     k_rec_init<<<(unsigned)nb, 256, 0, s>>>(rec, L, R, t, corr);
     if (L >= 256 && L % 256 == 0) {
         int64_t mb = (g.nw / 4 + 255) / 256;
-        if (mb > 152 * 8) mb = 152 * 8;
+        if (mb > (int64_t)device_sms() * 8) mb = (int64_t)device_sms() * 8;
         k_mb4<<<dim3((unsigned)mb, (unsigned)R), 256, 0, s>>>(lat, g, rec);
     } else {
         int64_t mb = (g.nw + 255) / 256;
-        if (mb > 152 * 8) mb = 152 * 8;
+        if (mb > (int64_t)device_sms() * 8) mb = (int64_t)device_sms() * 8;
         k_mb<<<dim3((unsigned)mb, (unsigned)R), 256, 0, s>>>(lat, g, rec);
     }
     int n = 2;

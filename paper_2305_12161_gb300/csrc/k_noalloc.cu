@@ -56,7 +56,8 @@ extern "C" int ising_measure_derived_noalloc(const uint32_t *lattice, int L, int
                                              unsigned flags, double *derived, void *stream)
 {
     if (!lattice || !derived || replicas < 1 || !packed_size_ok(L) || L > 4096) return ISING_EINVAL;
-    if (flags & ~(ISING_MEAS_CONNECTED | ISING_MEAS_NO_CORR)) return ISING_EINVAL;
+    // ISING_MEAS_DEVICE is accepted and ignored: the output is always device memory here
+    if (flags & ~(ISING_MEAS_DEVICE | ISING_MEAS_CONNECTED | ISING_MEAS_NO_CORR)) return ISING_EINVAL;
     const int64_t RL = 3 + 3 * (int64_t)(L / 2 + 1);
     if ((int64_t)replicas * RL > ISING_NOALLOC_MAX_RECORD_WORDS) return ISING_EINVAL;
     int64_t *records = nullptr;

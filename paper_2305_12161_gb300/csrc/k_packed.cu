@@ -473,13 +473,13 @@ SweepConfig default_sweep_config(int L, int R)
         int tz = 32;
         while (tz > 1 && L % tz != 0) tz >>= 1;
         // keep at least ~4 CTAs per SM-worth of tiles on small lattices
-        while (tz > 4 && (int64_t)(L / ty) * (L / tz) * R < 4 * 152) tz >>= 1;
+        while (tz > 4 && (int64_t)(L / ty) * (L / tz) * R < 4 * device_sms()) tz >>= 1;
         c = SweepConfig{VARIANT_ZMARCH, ty, tz, 0};
         if (!sweep_config_valid(L, c)) c = SweepConfig{VARIANT_WORD, 0, 0, 0};
         if (zfast_width_ok(L)) {
             const int fty = 256 / W4;
             int ftz = 32;
-            while (ftz > 4 && (int64_t)(L / fty) * (L / ftz) * R < 4 * 152) ftz >>= 1;
+            while (ftz > 4 && (int64_t)(L / fty) * (L / ftz) * R < 4 * device_sms()) ftz >>= 1;
             const SweepConfig f{VARIANT_ZFAST, fty, ftz, 2};
             if (sweep_config_valid(L, f)) c = f;
         }
@@ -533,7 +533,7 @@ static cudaError_t half_sweep_rule(uint32_t *lat, int L, int R, uint64_t seed, i
         k_sweep_zmarch<RULE><<<grid, cfg.tile_y * W4, smem, s>>>(lat, g, q, t, seed, cfg.tile_y, cfg.tile_z);
         return cudaGetLastError();
     }
-    const dim3 grid((unsigned)grid_for(g.nw, 256, 8 * 152 * 4), (unsigned)R);
+    const dim3 grid((unsigned)grid_for(g.nw, 256, 8 * (int64_t)device_sms() * 4), (unsigned)R);
     k_sweep_word<RULE><<<grid, 256, 0, s>>>(lat, g, q, t, seed);
     return cudaGetLastError();
 }

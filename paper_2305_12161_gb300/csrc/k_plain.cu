@@ -94,7 +94,7 @@ cudaError_t launch_init_plain(int8_t *plain, int L, int R, uint64_t seed, cudaSt
     const Geom g = make_geom(L);
     const int64_t warps = 2 * g.nw;
     int64_t blocks = (warps + 7) / 8;
-    if (blocks > 152 * 64) blocks = 152 * 64;
+    if (blocks > (int64_t)device_sms() * 64) blocks = (int64_t)device_sms() * 64;
     k_init_plain<<<dim3((unsigned)blocks, (unsigned)R), 256, 0, s>>>(plain, g, seed);
     return cudaGetLastError();
 }
@@ -105,7 +105,7 @@ static void sweeps_plain_rule(int8_t *plain, const Geom &g, int R, uint64_t seed
 {
     const int64_t N = (int64_t)g.L * g.L * g.L;
     int64_t blocks = (g.nw + 7) / 8;
-    if (blocks > 152 * 64) blocks = 152 * 64;
+    if (blocks > (int64_t)device_sms() * 64) blocks = (int64_t)device_sms() * 64;
     for (int64_t k = 0; k < n; ++k) {
         const uint32_t t = (uint32_t)(t0 + k);
         for (int h = 0; h < 2; ++h)
@@ -170,7 +170,7 @@ cudaError_t launch_pack(const int8_t *plain, uint32_t *lat, int L, int R, cudaSt
 {
     const Geom g = make_geom(L);
     int64_t blocks = (2 * g.nw + 7) / 8;
-    if (blocks > 152 * 64) blocks = 152 * 64;
+    if (blocks > (int64_t)device_sms() * 64) blocks = (int64_t)device_sms() * 64;
     k_pack<<<dim3((unsigned)blocks, (unsigned)R), 256, 0, s>>>(plain, lat, g);
     return cudaGetLastError();
 }
@@ -179,7 +179,7 @@ cudaError_t launch_unpack(const uint32_t *lat, int8_t *plain, int L, int R, cuda
 {
     const Geom g = make_geom(L);
     int64_t blocks = (2 * g.nw + 7) / 8;
-    if (blocks > 152 * 64) blocks = 152 * 64;
+    if (blocks > (int64_t)device_sms() * 64) blocks = (int64_t)device_sms() * 64;
     k_unpack<<<dim3((unsigned)blocks, (unsigned)R), 256, 0, s>>>(lat, plain, g);
     return cudaGetLastError();
 }

@@ -73,6 +73,7 @@ def lib() -> ctypes.CDLL:
                 "ising_reinit": (ctypes.c_int, [vp, ctypes.c_uint64]),
                 "ising_init_menger": (ctypes.c_int, [vp, ctypes.c_int]),
                 "ising_record_len": (ctypes.c_int64, [ctypes.c_int]),
+                "ising_footprint_bytes": (ctypes.c_int64, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ising_opts)]),
                 "ising_measure": (ctypes.c_int, [vp, vp]),
                 "ising_measure_ex": (ctypes.c_int, [vp, vp, vp, ctypes.c_double, ctypes.c_uint]),
                 "ising_radial_bins": (ctypes.c_int64, [ctypes.c_int]),
@@ -165,6 +166,21 @@ def ising_radial_bins(L: int) -> int:
 
 def ising_packed_words(L: int) -> int:
     return int(lib().ising_packed_words(L))
+
+
+def ising_footprint_bytes(L: int, replicas: int = 1, **opts) -> int:
+    """Device bytes a context holds once it has measured (ising_footprint_bytes in the C
+    ABI); keyword options as for Ising(...).  -1 for arguments the context would refuse."""
+    o = ising_opts()
+    lib().ising_default_opts(ctypes.byref(o))
+    for k, v in opts.items():
+        if k == "block":
+            o.block_x, o.block_y, o.block_z = v
+        elif k in dict(ising_opts._fields_) and k != "stream":
+            setattr(o, k, v)
+        else:
+            raise TypeError(f"unknown option {k}")
+    return int(lib().ising_footprint_bytes(L, replicas, ctypes.byref(o)))
 
 
 def ising_variants() -> list[int]:
@@ -489,11 +505,12 @@ NOALLOC_MAX_RECORD_WORDS = 131072
 
 
 def ising_measure_derived_noalloc(lattice, L: int, replicas: int, derived, c: float = 0.5, connected: bool = False,
-                                  corr: bool = True, stream=None) -> int:
+                                  corr: bool = True, stream=None, device_flag: bool = False) -> int:
     """Derived observables of caller-owned packed lattices into a caller-owned device
     buffer, allocating nothing (for callers that may not allocate device memory).
-    Returns the C status code; the work is enqueued on ``stream`` without a sync."""
-    flags = (MEAS_CONNECTED if connected else 0) | (0 if corr else MEAS_NO_CORR)
+    Returns the C status code; the work is enqueued on ``stream`` without a sync.
+    ``device_flag`` also passes ISING_MEAS_DEVICE, which the entry point accepts and ignores."""
+    flags = (MEAS_CONNECTED if connected else 0) | (0 if corr else MEAS_NO_CORR) | (MEAS_DEVICE if device_flag else 0)
     return int(lib().ising_measure_derived_noalloc(_dev_ptr(lattice), L, replicas, c, flags, _dev_ptr(derived),
                                                    _stream_handle(stream)))
 

@@ -48,10 +48,30 @@ class Result:
 
 
 def footprint_bytes(L: int, replicas: int, K: int) -> int:
-    """Device memory a request holds: packed lattices, its record buffers."""
-    words = ising.ising_packed_words(L)
-    rl = ising.ising_record_len(L)
-    return replicas * (words * 4 + (K + 1) * (rl * 8 + 32))
+    """Device memory a request holds while it runs: its context as the library accounts it
+    (ising_footprint_bytes: packed lattices, records and, for L >= 512, the tensor-core
+    correlation scratch of L^3 bytes) plus the server's own result buffers for K
+    measured times (records and derived values of every replica)."""
+    ctx = ising.ising_footprint_bytes(L, replicas)
+    if ctx < 0:
+        raise ValueError(f"no context for L={L}, replicas={replicas}")
+    return ctx + K * replicas * (ising.ising_record_len(L) * 8 + 4 * 8)
+
+
+def admit(pending: list, n_active: int, used: float, budget: float, max_slots: int, footprint) -> tuple:
+    """Admission by HBM footprint: walk the pending requests in arrival order and admit
+    each one for which a slot is free and whose footprint fits in what is left of the
+    budget (a smaller request may pass a larger one that does not fit yet).  Returns
+    (admitted, still pending, bytes in use afterwards)."""
+    admitted, keep = [], []
+    for req in pending:
+        fp = footprint(req)
+        if n_active + len(admitted) < max_slots and used + fp <= budget:
+            admitted.append(req)
+            used += fp
+        else:
+            keep.append(req)
+    return admitted, keep, used
 
 
 def schedule_for(req: Request) -> list[int]:
@@ -103,15 +123,10 @@ class QuenchServer:
         self.pending.append(req)
 
     def _admit(self) -> None:
-        keep = []
-        for req in self.pending:
-            fp = footprint_bytes(req.L, req.replicas, req.K)
-            if len(self.active) < self.max_slots and self.used + fp <= self.budget:
-                self.active.append(_Active(req, self.now(), self.torch))
-                self.used += fp
-            else:
-                keep.append(req)
-        self.pending = keep
+        admitted, self.pending, self.used = admit(self.pending, len(self.active), self.used, self.budget,
+                                                  self.max_slots, lambda r: footprint_bytes(r.L, r.replicas, r.K))
+        for req in admitted:
+            self.active.append(_Active(req, self.now(), self.torch))
 
     def _issue(self, a: _Active) -> None:
         # one quantum: sweep towards the next measured time, measure when it is reached

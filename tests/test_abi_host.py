@@ -121,3 +121,30 @@ def test_batch_create_rejects_bad_arguments(lib):
     assert lib.ising_batch_create(ctypes.byref(h), 0, None, None, None, None) == ising.ISING_EINVAL
     assert lib.ising_batch_destroy(None) == ising.ISING_OK
     assert lib.ising_batch_sweep(None, 1) == ising.ISING_EINVAL
+
+
+def test_footprint_bytes_counts_every_buffer(lib):
+    # packed store L^3/8 bytes per replica (1 bit per spin), records (3 + 3(L/2+1)) int64 and
+    # 4 doubles per replica, a 16-byte status word; the tensor-core correlation scratch L^3
+    # bytes for L >= 512 by default (not for the bit-count method), the fused kernel's second
+    # store, and L^3 bytes per replica for the plain form
+    from paper_2305_12161_gb300 import ising
+
+    def expect(L, R, fused=False, plain=False, tensor=None):
+        tensor = (L >= 512) if tensor is None else tensor
+        rec = 8 * R * (3 + 3 * (L // 2 + 1)) + 32 * R + 16
+        lat = R * (L**3 // 8 if L >= 64 else 8 * L * L)  # L < 64: one padded 32-bit word per row
+        return lat * (2 if fused else 1) + rec + (R * L**3 if plain else 0) + (L**3 if tensor else 0)
+
+    for L, R in ((32, 1), (64, 16), (256, 8), (512, 1), (1024, 3), (2048, 1)):
+        assert ising.ising_footprint_bytes(L, R) == expect(L, R), (L, R)
+        assert ising.ising_footprint_bytes(L, R, corr=ising.CORR_POPCOUNT) == expect(L, R, tensor=False)
+        assert ising.ising_footprint_bytes(L, R, form=ising.FORM_PLAIN) == expect(L, R, plain=True)
+    assert ising.ising_footprint_bytes(256, 1, corr=ising.CORR_TENSOR) == expect(256, 1, tensor=True)
+    assert ising.ising_footprint_bytes(2048, 1, variant=ising.VARIANT_ZFUSE, tile_z=32, depth=3) == \
+        expect(2048, 1, fused=True)
+    # what ising_create_ex refuses
+    assert ising.ising_footprint_bytes(96, 1) == -1
+    assert ising.ising_footprint_bytes(64, 0) == -1
+    assert ising.ising_footprint_bytes(128, 1, variant=ising.VARIANT_ZFUSE) == -1
+    assert ising.ising_footprint_bytes(128, 1, corr=ising.CORR_TENSOR) == -1

@@ -1,12 +1,18 @@
 """Parity at the full workload sizes, where the oracle cannot replay whole runs.
 
 * 8 replicas of L=256 (seeds 1..8), 10^4 MCS, 40 log-spaced times: the first times are
-  replayed by the oracle outright; at late times the GPU state is handed to the oracle,
-  which recounts the record and advances one MCS.
-* One L=2048 lattice in the launch configuration the benchmark times: sampled sites of
-  the initial state against the addressed Philox bits, sampled sites of two sweeps (one
-  dense-tie, one late) against the oracle's site update, and M, B and sampled D_a(r)
-  recounted by the oracle from the full GPU state.
+  replayed by the oracle outright for every replica; at EVERY recorded time the oracle
+  recounts the whole record (M, B and all 3 x 129 D_a(r)) from every replica's GPU state;
+  at four spread times the GPU state one MCS earlier is handed to the oracle, which
+  advances it one MCS, and all spins must agree.
+* One L=2048 lattice in the launch configuration the benchmark times (autotuned sweep
+  kernel, tensor-core correlation): the whole initial state against the oracle's
+  T = infinity start; at t = 0, 3 and 2000 the whole record of the tensor-core path against
+  the bit-count path (a different algorithm, oracle-pinned in full at L <= 256) on the
+  same state, M and B recounted by the oracle, and D_a(r) recounted by the oracle at the
+  tile edges of the tensor-core path (tiles of 128 positions, super-tiles of 256); at
+  t = 3 (dense ties) and t = 2000 the whole state handed to the oracle, advanced one MCS
+  there, and compared with the GPU's next state site by site (8.6e9 spins).
 """
 import numpy as np
 import pytest
@@ -25,82 +31,93 @@ def ising():
     return m
 
 
-def test_L256_eight_replicas_ten_thousand_mcs(ising):
+def _rec_D(rec, L):
+    return np.asarray(rec[3:]).reshape(3, L // 2 + 1)
+
+
+def test_L256_eight_replicas_every_recorded_time(ising):
     L, R, seed = 256, 8, 1
     times = inputs.log_schedule(10_000, 40)
-    recs = []
+    handoff = {5, 17, 29, 39}  # indices into times: one-MCS oracle advance there
+    n_early = 6                # times[:n_early] replayed whole by the oracle
+    early = [oracle.run(L, seed, r, times[:n_early])[0] for r in range(R)]
     with ising.Ising(L, replicas=R, seed=seed) as q:
-        recs.append(q.measure())
+        rec = q.measure()
+        for r in range(R):
+            s = q.get_spins(r)
+            assert np.array_equal(s, oracle.init(L, seed, r)), r
+            assert np.array_equal(oracle.record(s, 0), rec[r]), r
+            assert np.array_equal(early[r][0], rec[r]), r
         t = 0
-        for tk in times:
-            q.sweep(tk - t)
+        for k, tk in enumerate(times):
+            prev = None
+            if k in handoff:
+                q.sweep(tk - 1 - t)
+                prev = [q.get_spins(r) for r in range(R)]
+                q.sweep(1)
+            else:
+                q.sweep(tk - t)
             t = tk
-            recs.append(q.measure())
-    recs = np.stack(recs, axis=1)  # [R, 41, RL]
-    # early times replayed whole by the oracle (replicas 0 and 7)
-    for r in (0, 7):
-        want, _ = oracle.run(L, seed, r, times[:4])
-        assert np.array_equal(recs[r, :5], want), r
-    # late times: hand the GPU state at t_k - 1 to the oracle, advance one MCS
-    for r, k in ((0, 25), (3, 39), (7, 39)):
-        tk = times[k]
-        with ising.Ising(L, replicas=1, seed=seed + r) as q:
-            q.sweep(tk - 1)
-            s = q.get_spins(0)
-            q.sweep(1)
-            gpu_next = q.get_spins(0)
-        oracle.sweeps(s, tk - 1, 1, seed + r)
-        assert np.array_equal(s, gpu_next), (r, tk)
-        assert np.array_equal(oracle.record(s, tk), recs[r, k + 1]), (r, tk)
+            rec = q.measure()
+            assert np.all(rec[:, 0] == tk)
+            for r in range(R):
+                s = q.get_spins(r)
+                assert np.array_equal(oracle.record(s, tk), rec[r]), (r, tk)
+                if k < n_early:
+                    assert np.array_equal(early[r][k + 1], rec[r]), (r, tk)
+                if prev is not None:
+                    oracle.sweeps(prev[r], tk - 1, 1, seed + r)
+                    assert np.array_equal(prev[r], s), (r, tk)
+            del prev
 
 
-def _sample_sites(L, n, q, rng):
-    z = rng.integers(0, L, n)
-    y = rng.integers(0, L, n)
-    x = 2 * rng.integers(0, L // 2, n) + ((y + z + q) & 1)
-    return (x + L * (y + L * z)).astype(np.int64), x, y, z
+# Distances at which the tensor-core path's tiling changes: 128-position tiles, 256-position
+# super-tiles, the half-lattice end; plus the first few and a spread of seeded interior ones.
+EDGE_LAGS = [0, 1, 2, 3, 127, 128, 129, 255, 256, 257, 383, 384, 385, 511, 512, 513, 767, 768, 769, 1023, 1024]
 
 
-def _check_sweep(A, B, L, t, S, rng, n=200_000):
-    """B must be one MCS of A at sweep index t: red sites from A's neighbours, blue
-    sites from the red-updated neighbours (B) and their own old value (A)."""
-    Af, Bf = A.reshape(-1), B.reshape(-1)
-    i0, *_ = _sample_sites(L, n, 0, rng)
-    i0 = np.unique(i0)
-    assert np.array_equal(oracle.update_sites(A, 0, t, S, i0), Bf[i0])
-    i1, *_ = _sample_sites(L, n, 1, rng)
-    i1 = np.unique(i1)
-    got = Bf[i1].copy()
-    Bf[i1] = Af[i1]  # old values at the sampled blue sites; their neighbours are red
-    try:
-        assert np.array_equal(oracle.update_sites(B, 1, t, S, i1), got)
-    finally:
-        Bf[i1] = got
+def _lags_for(t_hand):
+    if t_hand < 2000:
+        return EDGE_LAGS
+    extra = np.random.default_rng(2048).choice(np.arange(4, 1023), size=24, replace=False)
+    return sorted(set(EDGE_LAGS) | set(int(v) for v in extra))
 
 
-def test_L2048_bench_configuration_sampled(ising):
+def _check_record(ising, q, qp, A, t_hand, L):
+    """Tensor-core record of q's state == bit-count record of the same state (qp), and
+    oracle recounts of M, B and D_a(r) at the lags of _lags_for."""
+    rec = q.measure()[0]
+    qp.set_packed(q.get_packed(0))
+    qp.t = q.t
+    recp = qp.measure()[0]
+    assert np.array_equal(rec, recp), (t_hand, np.flatnonzero(rec != recp)[:8])
+    M, B = oracle.magnetisation_bonds(A)
+    assert (int(rec[0]), int(rec[1]), int(rec[2])) == (t_hand, M, B), t_hand
+    lags = _lags_for(t_hand)
+    D = _rec_D(rec, L)
+    want = oracle.corr_lags(A, lags)
+    for j, r in enumerate(lags):
+        assert list(D[:, r]) == list(want[j]), (t_hand, r)
+
+
+def test_L2048_bench_configuration_full(ising):
     L, S = 2048, 1
-    rng = np.random.default_rng(2048)
-    with ising.Ising(L, replicas=1, seed=S) as q:
-        # initial state: sampled sites against the addressed Philox bit (phase 2 + q)
+    tuned = ising.ising_tune_sweep(L, 1, probe_mcs=8)
+    kw = dict(variant=tuned["variant"], tile_y=tuned["tile_y"], tile_z=tuned["tile_z"], depth=tuned["depth"])
+    with ising.Ising(L, replicas=1, seed=S, **kw) as q, \
+            ising.Ising(L, replicas=1, seed=S, corr=ising.CORR_POPCOUNT) as qp:
+        # whole initial state against the oracle's T = infinity start
         A = q.get_spins(0)
-        for qq in (0, 1):
-            idx, x, y, z = _sample_sites(L, 2000, qq, rng)
-            h = (x >> 1) + (L // 2) * (y + L * z)
-            want = np.array([1 if oracle.rng_bit(S, 0, 2 + qq, int(hh)) else -1 for hh in h], dtype=np.int8)
-            assert np.array_equal(A.reshape(-1)[idx], want)
+        assert np.array_equal(A, oracle.init(L, S, 0))
+        _check_record(ising, q, qp, A, 0, L)
+        del A
         for t_hand in (3, 2000):
             q.sweep(t_hand - q.t)
             A = q.get_spins(0)
-            rec = q.measure()[0]
+            _check_record(ising, q, qp, A, t_hand, L)
             q.sweep(1)
             B = q.get_spins(0)
-            _check_sweep(A, B, L, t_hand, S, rng)
-            # observables of the handed-over state
-            M, Bnd = oracle.magnetisation_bonds(A)
-            assert (rec[1], rec[2]) == (M, Bnd), t_hand
-            H = L // 2
-            for r in (1, 2, 17, 1024):
-                D = oracle.corr_lag(A, r)
-                assert [rec[3 + r], rec[3 + (H + 1) + r], rec[3 + 2 * (H + 1) + r]] == list(D), (t_hand, r)
-            del A, B
+            oracle.sweeps(A, t_hand, 1, S)
+            eq = A == B
+            assert eq.all(), (t_hand, int((~eq).sum()))
+            del A, B, eq

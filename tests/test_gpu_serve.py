@@ -40,3 +40,19 @@ def test_oversized_request_rejected(serve):
     srv = serve.QuenchServer(budget_bytes=1e6)
     with pytest.raises(ValueError):
         srv.submit(serve.Request(id=0, L=256, t_max=10, replicas=1, seed=1))
+
+
+def test_correlation_scratch_forces_queueing(serve):
+    # both L = 512 lattices fit the budget, but only one tensor-core correlation scratch
+    # (512^3 bytes) does: the second request waits until the first has retired
+    reqs = [serve.Request(id=i, L=512, t_max=30, replicas=1, seed=70 + i, arrival_s=0.0, K=3) for i in range(2)]
+    fp = serve.footprint_bytes(512, 1, 3)
+    budget = fp + 2 * 512**3 // 8
+    srv = serve.QuenchServer(budget_bytes=budget, max_slots=4, quantum_mcs=8)
+    res = {r.request.id: r for r in srv.run(reqs)}
+    first, second = sorted(res.values(), key=lambda r: r.admitted_s)
+    assert second.admitted_s >= first.finished_s
+    assert srv.used == 0
+    for r in res.values():
+        alone = serve.run_alone(r.request)
+        assert np.array_equal(r.records, alone.records)
