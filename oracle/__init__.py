@@ -92,6 +92,12 @@ def lib() -> ctypes.CDLL:
             L.orc_sweeps_mixed.argtypes = [ctypes.c_int, i8p, ctypes.c_uint32, ctypes.c_int64,
                                            ctypes.c_uint64, ctypes.c_int]
             L.orc_sweeps_mixed.restype = None
+            L.orc_rsf_draw.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int64, ctypes.c_int64, i64p,
+                                       ctypes.POINTER(ctypes.c_int)]
+            L.orc_rsf_draw.restype = None
+            L.orc_sweeps_rsf.argtypes = [ctypes.c_int, i8p, ctypes.c_uint32, ctypes.c_int64, ctypes.c_uint64,
+                                         ctypes.c_int, i64p, i64p]
+            L.orc_sweeps_rsf.restype = ctypes.c_int64
             L.orc_dcb_valid.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
             L.orc_dcb_valid.restype = ctypes.c_int
             L.orc_dcb_fine_first.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int64]
@@ -197,6 +203,25 @@ def mixed_order(S: int, t: int) -> int:
 def sweeps_mixed(s: np.ndarray, t0: int, n: int, S: int, rule: int = TIE_GLAUBER) -> None:
     L = _check_lattice(s)
     lib().orc_sweeps_mixed(L, _p(s, ctypes.c_int8), t0, n, S % 2**64, rule)
+
+
+def rsf_draw(S: int, t: int, k: int, N: int):
+    """(site, zero-energy bit) of step k of rsf sweep t."""
+    i = ctypes.c_int64(0)
+    b = ctypes.c_int(0)
+    lib().orc_rsf_draw(S % 2**64, t, k, N, ctypes.byref(i), ctypes.byref(b))
+    return int(i.value), int(b.value)
+
+
+def sweeps_rsf(s: np.ndarray, t0: int, n: int, S: int, rule: int = TIE_GLAUBER):
+    """``n`` random-site-flip sweeps in place (N sequential proposals each); returns
+    (flips, incremental dB, incremental dM).  Sequential: releases the GIL while it runs,
+    so independent lattices can be advanced from several Python threads."""
+    L = _check_lattice(s)
+    dB = ctypes.c_int64(0)
+    dM = ctypes.c_int64(0)
+    f = lib().orc_sweeps_rsf(L, _p(s, ctypes.c_int8), t0, n, S % 2**64, rule, ctypes.byref(dB), ctypes.byref(dM))
+    return int(f), int(dB.value), int(dM.value)
 
 
 def dcb_valid(L: int, block) -> bool:

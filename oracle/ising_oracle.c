@@ -429,6 +429,81 @@ void orc_sweeps_mixed(int L, int8_t *s, uint32_t t0, int64_t n, uint64_t S, int 
 }
 
 /* ------------------------------------------------------------------------------ */
+/* Random-site-flip (rsf) update (Methods, "Random-site-flip update"): one MC step picks a
+ * site uniformly at random and proposes to flip it; the flip is accepted with Eq. (6) at
+ * T -> 0 (always if dE < 0, never if dE > 0, with probability 1/2 if dE = 0, or per the
+ * rule flag); N = L^3 steps are one MCS.  The steps are sequential: each one sees every
+ * flip before it, and within a sweep a site may be proposed several times or not at all.
+ * This is the paper's baseline dynamics, against which the checkerboard's time is
+ * rescaled (Supplementary Table of time factors: checkerboard 1.75, rsf 1).
+ *
+ * Random numbers (the paper names no generator): step k (0 <= k < N) of sweep t (0-based)
+ * takes one Philox4x32-10 call with counter (lo32 k, t, 7, hi32 k) and key (lo32 S, hi32 S);
+ * the site is the 64-bit integer o[1]:o[0] modulo N (bias at most N / 2^64) and the
+ * zero-energy decision is bit 0 of o[2]. */
+void orc_rsf_draw(uint64_t S, uint32_t t, int64_t k, int64_t N, int64_t *site_out, int *bit_out)
+{
+    uint32_t ctr[4] = {(uint32_t)((uint64_t)k & 0xffffffffu), t, 7u, (uint32_t)((uint64_t)k >> 32)};
+    uint32_t key[2] = {(uint32_t)(S & 0xffffffffu), (uint32_t)(S >> 32)};
+    uint32_t o[4];
+    orc_philox4x32_10(ctr, key, o);
+    const uint64_t r = ((uint64_t)o[1] << 32) | (uint64_t)o[0];
+    *site_out = (int64_t)(r % (uint64_t)N);
+    *bit_out = (int)(o[2] & 1u);
+}
+
+/* n rsf sweeps in place from completed-sweep count t0.  Returns the number of accepted
+ * flips; *dB receives the change of the broken-bond count accumulated flip by flip (a
+ * flipped site with a aligned neighbours before the flip changes B by 2a - 6), *dM that
+ * of the magnetisation. */
+int64_t orc_sweeps_rsf(int L_, int8_t *s, uint32_t t0, int64_t n, uint64_t S, int rule, int64_t *dB, int64_t *dM)
+{
+    const int64_t L = L_;
+    const int64_t N = L * L * L;
+    int64_t flips = 0, db = 0, dm = 0;
+    for (int64_t sweep = 0; sweep < n; ++sweep) {
+        const uint32_t t = t0 + (uint32_t)sweep;
+        for (int64_t k = 0; k < N; ++k) {
+            int64_t i;
+            int bit;
+            orc_rsf_draw(S, t, k, N, &i, &bit);
+            const int64_t x = i % L, y = (i / L) % L, z = i / (L * L);
+            const int8_t nb[6] = {
+                s[site(L, wrap(x + 1, L), y, z)], s[site(L, wrap(x - 1, L), y, z)],
+                s[site(L, x, wrap(y + 1, L), z)], s[site(L, x, wrap(y - 1, L), z)],
+                s[site(L, x, y, wrap(z + 1, L))], s[site(L, x, y, wrap(z - 1, L))]};
+            const int8_t old = s[i];
+            int u = 0, a = 0;
+            for (int j = 0; j < 6; ++j) {
+                u += (nb[j] == 1);
+                a += (nb[j] == old);
+            }
+            /* dE = 2 old (2u - 6): accept for dE < 0, reject for dE > 0, tie at u = 3 */
+            int8_t nw;
+            if (u >= 4)
+                nw = 1;
+            else if (u <= 2)
+                nw = -1;
+            else if (rule == ORC_TIE_ALWAYS)
+                nw = (int8_t)-old;
+            else if (rule == ORC_TIE_NEVER)
+                nw = old;
+            else
+                nw = bit ? (int8_t)-old : old;
+            if (nw != old) {
+                s[i] = nw;
+                flips += 1;
+                db += 2 * a - 6;
+                dm += (int64_t)nw - (int64_t)old;
+            }
+        }
+    }
+    if (dB) *dB = db;
+    if (dM) *dM = dm;
+    return flips;
+}
+
+/* ------------------------------------------------------------------------------ */
 /* Double-checkerboard update (Supp. Methods I A: Weigel's GPU domain decomposition,
  * generalised to d = 3).  The lattice is cut into blocks of bx*by*bz sites; block
  * (i, j, k) = (x / bx, y / by, z / bz) is red (colour 0) when i + j + k is even and blue
