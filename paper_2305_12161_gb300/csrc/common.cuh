@@ -201,7 +201,10 @@ __device__ __forceinline__ uint32_t maj3(uint32_t a, uint32_t b, uint32_t c) { r
 // group has u = 3, i.e. s1 != s2 and c1 != c2.  For Glauber, COMPACT first reduces the adders
 // to the masks [u >= 4] and [u = 3] (count6), which keeps two words per word live across the
 // Philox call instead of four, at one more logic operation per word.
-template <int RULE, bool COMPACT = true>
+// LAZY (the default) draws Philox only for a group with a tie; without it every group draws
+// (a warp draws whenever one of its 32 groups has a tie, which is nearly always, so the tie
+// test then only costs instructions).
+template <int RULE, bool COMPACT = true, bool LAZY = true>
 __device__ __forceinline__ uint4 new_spins4(const uint4 &s, const uint4 &C, const uint4 &X, const uint4 &ym,
                                             const uint4 &yp, const uint4 &zm, const uint4 &zp, uint32_t group,
                                             uint32_t t, uint32_t q, const PhiloxKeys &keys)
@@ -227,10 +230,14 @@ __device__ __forceinline__ uint4 new_spins4(const uint4 &s, const uint4 &C, cons
     const uint32_t s2w = yp.w ^ zm.w ^ zp.w, c2w = maj3(yp.w, zm.w, zp.w);
     uint4 tau;
     if (RULE == TIE_GLAUBER) {
-        const uint32_t tie = ((s1x ^ s2x) & (c1x ^ c2x)) | ((s1y ^ s2y) & (c1y ^ c2y)) |
-                             ((s1z ^ s2z) & (c1z ^ c2z)) | ((s1w ^ s2w) & (c1w ^ c2w));
         U4 o{0u, 0u, 0u, 0u};
-        if (tie != 0u) o = philox4x32_10_rk(group, t, q, 0u, keys);
+        if (LAZY) {
+            const uint32_t tie = ((s1x ^ s2x) & (c1x ^ c2x)) | ((s1y ^ s2y) & (c1y ^ c2y)) |
+                                 ((s1z ^ s2z) & (c1z ^ c2z)) | ((s1w ^ s2w) & (c1w ^ c2w));
+            if (tie != 0u) o = philox4x32_10_rk(group, t, q, 0u, keys);
+        } else {
+            o = philox4x32_10_rk(group, t, q, 0u, keys);
+        }
         tau = make_uint4(s.x ^ o.x, s.y ^ o.y, s.z ^ o.z, s.w ^ o.w);
     } else if (RULE == TIE_ALWAYS) {
         tau = make_uint4(~s.x, ~s.y, ~s.z, ~s.w);

@@ -395,7 +395,7 @@ int ising_sweep(ising_ctx *c, int64_t n)
                                 &c->launches);
     else if (c->cfg.variant == VARIANT_ZFUSE)
         e = launch_sweeps_fused(&c->lat, &c->lat_alt, c->L, c->R, c->seed, c->opts.tie, c->t, n, c->opts.cycle,
-                                c->cfg.tile_z, c->cfg.depth, c->stream, &c->launches);
+                                c->cfg.tile_z, c->cfg.depth, c->dev_err, c->wait_timeout_s, c->stream, &c->launches);
     else
         e = launch_sweeps_packed(c->lat, c->L, c->R, c->seed, c->opts.tie, c->t, n, c->opts.cycle, c->cfg, c->stream,
                                  &c->launches);
@@ -412,7 +412,8 @@ static int check_device_waits(ising_ctx *c)
     int h = 0;
     CK(c, cudaMemcpyAsync(&h, c->dev_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
-    if (h) return fail(c, ISING_ETIMEOUT, "tensor-core correlation: a bounded device-side wait gave up");
+    if (h == 4) return fail(c, ISING_ETIMEOUT, "fused sweep: a bounded wait for a copy gave up");
+    if (h) return fail(c, ISING_ETIMEOUT, "tensor-core correlation: a bounded device-side wait gave up (code %d)", h);
     return ISING_OK;
 }
 
@@ -723,7 +724,7 @@ int ising_tune_sweep(int L, int replicas, int probe_mcs, const ising_opts *base,
             }
         }
         for (int tz : {16, 32, 64, 128})
-            for (int mb : {2, 3, 10, 11}) {
+            for (int mb : {1, 2, 3, 10, 11}) {
                 const SweepConfig cf{VARIANT_ZFUSE, 256 / W4, tz, mb};
                 if (sweep_config_valid(L, cf)) cands.push_back(cf);
             }

@@ -16,6 +16,8 @@
 // N/4 bytes, against 3 N/8 for two half-sweeps.  Two tilings: k_mcs_fused (tiles of
 // 256 / W4 rows, the halo rows of A on extra lanes of warp 0) and k_mcs_fused_bal (256 / W4
 // computed rows of which the outer two are the halo, so every warp does the same work).
+#include <type_traits>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -56,89 +58,134 @@ __device__ __forceinline__ uint4 xshift(const uint4 &C, uint32_t edge_left_w, ui
 
 }  // namespace
 
+// Bounded wait on phase `parity` of an mbarrier: spins on try_wait until the phase has
+// completed or timeout_ns of %globaltimer have passed (with a cap on rounds as a backstop);
+// false when it gave up.
+__device__ __forceinline__ uint64_t fused_timer_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ bool fused_mbar_wait(uint32_t addr, uint32_t parity, uint64_t timeout_ns)
+{
+    uint32_t done = 0;
+    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(done)
+                 : "r"(addr), "r"(parity)
+                 : "memory");
+    if (done) return true;
+    const uint64_t t0 = fused_timer_ns();
+    for (int it = 0; it < (1 << 28); ++it) {
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(done)
+                     : "r"(addr), "r"(parity)
+                     : "memory");
+        if (done) return true;
+        if ((it & 63) == 63 && fused_timer_ns() - t0 > timeout_ns) return false;
+    }
+    return false;
+}
+
+// Bulk copy (TMA, non-tensor) of `bytes` from global to shared memory, completing on mbarrier
+// `mbar`; both addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void fused_bulk(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(dst), "l"(src), "r"(bytes), "r"(mbar)
+                 : "memory");
+}
+
+// Arguments of one launch (one replica): kernel parameter space, so the Philox round keys
+// are read as constant-bank operands of the round's logic operations and take no registers.
+struct FusedArgs {
+    PhiloxKeys keys;           // round keys of the replica's Philox key (seed + replica)
+    const uint4 *Acur, *Bcur;  // store of sweep t: first-updated sublattice A and the other, B
+    uint4 *Anxt, *Bnxt;        // store of sweep t + 1
+    int L, TZ;
+    uint32_t t, A;             // sweep index, first sublattice (its tie-bit phase)
+    int *err;                  // set to 4 when a bounded wait gave up
+    uint64_t timeout_ns;
+};
+
 // Shared memory: NS copy slots, each one B plane (rows y0-2 .. y0+TY+1) and one old-A plane
-// (rows y0-1 .. y0+TY); two slots of new A (rows y0-1 .. y0+TY).
+// (rows y0-1 .. y0+TY); three slots of new A (rows y0-1 .. y0+TY); NS mbarriers.
 template <int W4, int NS>
 static constexpr size_t fused_smem_bytes()
 {
     constexpr int TY = 256 / W4;
-    return sizeof(uint4) * (size_t)(NS * (2 * TY + 6) * W4 + 2 * (TY + 2) * W4);
+    return sizeof(uint4) * (size_t)(NS * (2 * TY + 6) * W4 + 3 * (TY + 2) * W4) + 8 * NS;
 }
 
 // Thread tid owns column cx = lane % W4 of row y0 + ty (the rows of a warp share their parity,
-// as in the half-sweep kernel) for both sublattices, so the B update finds its own column's
-// new A on planes zB - 1, zB, zB + 1 in registers and reads only rows y +- 1 from shared memory.
-// x-edge words come from the neighbouring lane of the row by a shuffle.  Lanes 0 .. 2 W4 - 1
-// of warp 0 also update A on the halo rows.  Copy group g brings B plane z0 - 2 + g and, for
-// g >= 2, old-A plane z0 - 1 + (g - 2); step k reads the slots of groups k .. k + 2 and
-// refills the slot of group k - 1 with group k + NS - 1, so NS - 3 groups stay in flight.
+// as in the half-sweep kernel) for both sublattices.  Copy group g (one TMA bulk copy per
+// contiguous run of rows, issued by thread 0, completing on the mbarrier of slot g % NS)
+// brings B plane z0 - 2 + g and, for g >= 2, old-A plane z0 - 1 + (g - 2); step k reads the
+// slots of groups k, k + 1, k + 2 and, after the step's barrier, thread 0 refills the slot of
+// group k - 1 with group k - 1 + NS, so NS - 3 groups stay in flight.  Every operand of a
+// step comes from shared memory (nothing is carried across steps in registers), and the
+// steps are unrolled in pairs so that the x direction P of the pair's two planes is a
+// compile-time constant.  Lanes 0 .. 2 W4 - 1 of warp 0 also update A on the halo rows.
 // Offsets into a sublattice are 32-bit uint4 indices (L^3 / 256 < 2^31).
-template <int RULE, int W4, int NS>
-__global__ void __launch_bounds__(256, 3) k_mcs_fused(const uint32_t *__restrict__ cur, uint32_t *__restrict__ nxt,
-                                                      Geom g, int mixed, uint32_t t, uint64_t seed, int TZ)
+template <int RULE, int W4, int NS, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_mcs_fused(const __grid_constant__ FusedArgs fa)
 {
     constexpr int NT = 256, TY = NT / W4, RW = 32 / W4;
     constexpr int RB = TY + 4;                 // B rows of a slot
     constexpr int RA = TY + 2;                 // A rows of a slot, and of a new-A slot
     constexpr int NB = RB * W4;                // B items of a slot (A items follow)
     constexpr int SLOT = (RB + RA) * W4;
-    constexpr int NCP = (SLOT + NT - 1) / NT;  // copies per thread per group
+    constexpr int NEW = RA * W4;               // items of a new-A slot
     constexpr uint32_t FULL = 0xffffffffu;
     constexpr uint32_t HMASK = 2 * W4 >= 32 ? FULL : ((1u << (2 * W4)) - 1u);
-    extern __shared__ uint4 fsm[];
-    uint4 *ring = fsm;              // [NS][SLOT], group g in slot g % NS
-    uint4 *anew = fsm + NS * SLOT;  // [2][RA * W4]
-    const int L = g.L;
+    extern __shared__ __align__(16) uint4 fsm[];
+    uint4 *ring = fsm;                   // [NS][SLOT], group g in slot g % NS
+    uint4 *anew = fsm + NS * SLOT;       // [3][NEW], plane zA in slot k % 3
+    uint64_t *full = reinterpret_cast<uint64_t *>(anew + 3 * NEW);  // [NS]
+    const int L = fa.L, TZ = fa.TZ;
     const int tid = threadIdx.x;
     const int nty = L / TY;
     const int y0 = (int)(blockIdx.x % nty) * TY;
     const int z0 = (int)(blockIdx.x / nty) * TZ;
-    const int r = blockIdx.y;
-    const uint64_t S = seed + (uint64_t)r;
-    // sublattice updated first: 0 (01 cycle) or the sweep's drawn order (mixed cycle)
-    int A = 0;
-    if (mixed) A = (int)(philox4x32_10(0u, t, 5u, 0u, (uint32_t)S, (uint32_t)(S >> 32)).x & 1u);
-    const int B = 1 - A;
     const int32_t plane4 = L * W4;
     const int32_t vol4 = L * plane4;
-    const uint4 *Acur = reinterpret_cast<const uint4 *>(cur + (2 * (int64_t)r + A) * g.nw);
-    const uint4 *Bcur = reinterpret_cast<const uint4 *>(cur + (2 * (int64_t)r + B) * g.nw);
-    uint4 *Anxt = reinterpret_cast<uint4 *>(nxt + (2 * (int64_t)r + A) * g.nw);
-    uint4 *Bnxt = reinterpret_cast<uint4 *>(nxt + (2 * (int64_t)r + B) * g.nw);
-    const PhiloxKeys keys = philox_keys(S);
     auto wrapL = [&](int a) { return a < 0 ? a + L : (a >= L ? a - L : a); };
+    const uint32_t full0 = (uint32_t)__cvta_generic_to_shared(full);
+    const uint32_t ring0 = (uint32_t)__cvta_generic_to_shared(ring);
 
-    // copies: slot item e = tid + j NT; its offset within a plane is fixed over the march
-    int32_t coff[NCP];
-#pragma unroll
-    for (int j = 0; j < NCP; ++j) {
-        const int e = tid + j * NT;
-        const int ea = e < NB ? e : e - NB;
-        coff[j] = wrapL(y0 + ea / W4 - (e < NB ? 2 : 1)) * W4 + (ea & (W4 - 1));
-    }
-    int32_t ob = wrapL(z0 - 2) * plane4;  // B plane of the next group
-    int32_t oa = wrapL(z0 - 1) * plane4;  // A plane of the next group that has one
-    auto issue = [&](int gi, int slot) {
-        uint4 *dst = ring + slot * SLOT;
-        if (gi <= TZ + 3) {
-            const bool wa = gi >= 2;
-#pragma unroll
-            for (int j = 0; j < NCP; ++j) {
-                const int e = tid + j * NT;
-                if (e < NB)
-                    fcp16(dst + e, Bcur + (ob + coff[j]));
-                else if (e < SLOT && wa)
-                    fcp16(dst + e, Acur + (oa + coff[j]));
-            }
-            ob += plane4;
-            if (ob == vol4) ob = 0;
-            if (wa) {
-                oa += plane4;
-                if (oa == vol4) oa = 0;
-            }
+    // thread 0: rows ystart .. ystart + n - 1 of the plane at `src` (wrapped in y) into dst, one
+    // bulk copy per run of consecutive rows (up to three when the tile spans the whole plane)
+    auto copy_rows = [&](uint32_t dst, const uint4 *src, int ystart, int n, uint32_t mbar) {
+        int row = wrapL(ystart);
+        while (n > 0) {
+            const int m = min(n, L - row);
+            fused_bulk(dst, src + row * W4, (uint32_t)(m * W4 * 16), mbar);
+            dst += (uint32_t)(m * W4 * 16);
+            n -= m;
+            row = 0;
         }
-        fcommit();
     };
+    int g_issued = -1;  // thread 0: last group issued
+    auto issue = [&](int g) {  // thread 0
+        if (g > TZ + 3) return;
+        g_issued = g;
+        const int sl = g % NS;
+        const uint32_t mbar = full0 + 8u * (uint32_t)sl;
+        const uint32_t bytes = (uint32_t)(16 * (NB + (g >= 2 ? RA * W4 : 0)));
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+        const uint32_t dst = ring0 + (uint32_t)(16 * sl * SLOT);
+        copy_rows(dst, fa.Bcur + wrapL(z0 - 2 + g) * plane4, y0 - 2, RB, mbar);
+        if (g >= 2) copy_rows(dst + 16u * NB, fa.Acur + wrapL(z0 - 3 + g) * plane4, y0 - 1, RA, mbar);
+    };
+    if (tid == 0) {
+        for (int i = 0; i < NS; ++i)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(full0 + 8u * (uint32_t)i));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid == 0)
+        for (int g = 0; g < NS; ++g) issue(g);
 
     const int warp = tid >> 5, lane = tid & 31;
     const int cx = lane & (W4 - 1);
@@ -153,67 +200,89 @@ __global__ void __launch_bounds__(256, 3) k_mcs_fused(const uint32_t *__restrict
     const int hB = (hr ? TY + 2 : 1) * W4 + cx;  // halo row in a B slot
     const int hN = (hr ? TY + 1 : 0) * W4 + cx;  // halo row in an A slot
     const int32_t dh = wrapL(hr ? y0 + TY : y0 - 1) * W4 + cx - own;
+    const uint32_t A = fa.A, B = 1u - fa.A;
 
-#pragma unroll 1
-    for (int gi = 0; gi < NS - 1; ++gi) issue(gi, gi);
+    // groups 0 and 1 before the first step (step k waits for group k + 2); thread 0 tracks
+    // the last group it saw land and the last it issued, for the drain after a failed wait
+    bool bad = !fused_mbar_wait(full0, 0u, fa.timeout_ns);
+    bad |= !fused_mbar_wait(full0 + 8u, 0u, fa.timeout_ns);
+    int g_done = bad ? -1 : 1;
     int32_t oA = wrapL(z0 - 1) * plane4 + own;  // plane zA, own column
-    int32_t oB = 0;                             // plane zA - 1 (= zB), own column
-    int p = (ty + z0 - 1 + A) & 1;              // x direction on plane zA (y0 even); also B's on zA - 1
-    fwait<NS - 3>();  // groups 0 and 1
-    __syncthreads();
-    uint4 bm = ring[0 * SLOT + rB];  // B plane zA - 1, own column
-    uint4 bc = ring[1 * SLOT + rB];  // B plane zA
-    uint4 a1 = make_uint4(0u, 0u, 0u, 0u), a2 = a1;  // new A, planes zA - 1 and zA - 2, own column
-    int sl0 = 0;  // slot of group k
-#pragma unroll 1
-    for (int k = 0; k <= TZ + 1; ++k) {
-        fwait<NS - 4>();  // group k + 2 has landed
-        __syncthreads();
-        const int sl1 = sl0 == NS - 1 ? 0 : sl0 + 1, sl2 = sl1 == NS - 1 ? 0 : sl1 + 1;
-        issue(k + NS - 1, sl0 == 0 ? NS - 1 : sl0 - 1);  // the slot of group k - 1, last read in step k - 1
-        const uint4 *Bsm = ring + sl0 * SLOT;  // B plane zA - 1
-        const uint4 *Bs0 = ring + sl1 * SLOT;  // B plane zA
-        const uint4 *Bsp = ring + sl2 * SLOT;  // B plane zA + 1, old A plane zA (at NB)
-        sl0 = sl1;
-        uint4 *An = anew + (k & 1) * RA * W4;
-        // A, own column
-        const uint4 bp = Bsp[rB];
+    // one step: A on plane zA = z0 - 1 + k (tile rows and halo rows), then B on zA - 1
+    auto step = [&](const int k, auto Pc) -> bool {
+        constexpr int P = decltype(Pc)::value;
+        const int g2 = k + 2;
+        bool fail = !fused_mbar_wait(full0 + 8u * (uint32_t)(g2 % NS), (uint32_t)((g2 / NS) & 1), fa.timeout_ns);
+        if (!fail) g_done = g2;
+        if (__syncthreads_or(fail)) return false;
+        if (tid == 0 && k >= 1) issue(k - 1 + NS);  // the slot of group k - 1, last read in step k - 1
+        const uint4 *S0 = ring + (k % NS) * SLOT;        // B plane zA - 1
+        const uint4 *S1 = ring + ((k + 1) % NS) * SLOT;  // B plane zA
+        const uint4 *S2 = ring + (g2 % NS) * SLOT;       // B plane zA + 1; old A plane zA at NB
+        uint4 *An = anew + (k % 3) * NEW;
+        const uint4 bm = S0[rB];
         uint4 a0;
         {
-            const uint32_t e = __shfl_sync(FULL, p ? bc.x : bc.w, p ? srcr : srcl, W4);
-            const uint4 X = xshift(bc, e, e, p);
-            a0 = new_spins4<RULE, false>(Bsp[NB + rN], bc, X, Bs0[rB - W4], Bs0[rB + W4], bm, bp, (uint32_t)oA, t,
-                               (uint32_t)A, keys);
+            const uint4 bc = S1[rB];
+            const uint32_t e = __shfl_sync(FULL, P ? bc.x : bc.w, P ? srcr : srcl, W4);
+            const uint4 X = xshift(bc, e, e, P);
+            a0 = new_spins4<RULE, false, false>(S2[NB + rN], bc, X, S1[rB - W4], S1[rB + W4], bm, S2[rB], (uint32_t)oA,
+                                         fa.t, A, fa.keys);
             An[rN] = a0;
-            if (k >= 1 && k <= TZ) Anxt[oA] = a0;
+            if (k >= 1 && k <= TZ) fa.Anxt[oA] = a0;
         }
         // A, halo rows: row y0 - 1 is odd (the other direction than warp 0's even rows), row
         // y0 + TY even (the same)
         if (hl) {
-            const uint4 hbc = Bs0[hB];
-            const int ph = p ^ 1 ^ hr;
+            const uint4 hbc = S1[hB];
+            const int ph = P ^ 1 ^ hr;
             const uint32_t e = __shfl_sync(HMASK, ph ? hbc.x : hbc.w, ph ? srcr : srcl, W4);
             const uint4 X = xshift(hbc, e, e, ph);
-            An[hN] = new_spins4<RULE, false>(Bsp[NB + hN], hbc, X, Bs0[hB - W4], Bs0[hB + W4], Bsm[hB], Bsp[hB],
-                                   (uint32_t)(oA + dh), t, (uint32_t)A, keys);
+            An[hN] = new_spins4<RULE, false, false>(S2[NB + hN], hbc, X, S1[hB - W4], S1[hB + W4], S0[hB], S2[hB],
+                                             (uint32_t)(oA + dh), fa.t, A, fa.keys);
         }
-        // B on plane zB = zA - 1, own column: new A of planes zB - 1, zB, zB + 1 are a2, a1, a0
+        // B on plane zB = zA - 1, own column: new A of planes zB - 1, zB, zB + 1 are in the
+        // new-A slots of steps k - 2 and k - 1, and a0
         if (k >= 2) {
-            const uint4 *Ap = anew + ((k - 1) & 1) * RA * W4;  // new A, plane zB
-            const uint32_t e = __shfl_sync(FULL, p ? a1.x : a1.w, p ? srcr : srcl, W4);
-            const uint4 X = xshift(a1, e, e, p);
-            Bnxt[oB] = new_spins4<RULE, false>(bm, a1, X, Ap[rN - W4], Ap[rN + W4], a2, a0, (uint32_t)oB, t, (uint32_t)B, keys);
+            const uint4 *A1 = anew + ((k + 2) % 3) * NEW;  // step k - 1: plane zB
+            const uint4 *A2 = anew + ((k + 1) % 3) * NEW;  // step k - 2: plane zB - 1
+            const uint4 a1 = A1[rN];
+            const uint32_t e = __shfl_sync(FULL, P ? a1.x : a1.w, P ? srcr : srcl, W4);
+            const uint4 X = xshift(a1, e, e, P);
+            const int32_t oB = oA >= plane4 ? oA - plane4 : oA - plane4 + vol4;
+            fa.Bnxt[oB] = new_spins4<RULE, false, false>(bm, a1, X, A1[rN - W4], A1[rN + W4], A2[rN], a0, (uint32_t)oB, fa.t,
+                                                  B, fa.keys);
         }
-        a2 = a1;
-        a1 = a0;
-        bm = bc;
-        bc = bp;
-        oB = oA;
         oA += plane4;
         if (oA >= vol4) oA -= vol4;
-        p ^= 1;
+        return true;
+    };
+    // x direction of A on plane zA at k = 0 (and of B on zA - 1): parity of ty + zA + A, ty's
+    // parity is the warp's; it alternates with k
+    const int p0 = ((warp & 1) + z0 - 1 + (int)A) & 1;
+    bool ok = !__syncthreads_or(bad);
+    if (ok) {
+        // TZ + 2 steps in pairs; for odd TZ the last pair has one step
+        if (p0) {
+#pragma unroll 1
+            for (int k = 0; k <= TZ + 1 && ok; k += 2)
+                ok = step(k, std::integral_constant<int, 1>{}) &&
+                     (k + 1 > TZ + 1 || step(k + 1, std::integral_constant<int, 0>{}));
+        } else {
+#pragma unroll 1
+            for (int k = 0; k <= TZ + 1 && ok; k += 2)
+                ok = step(k, std::integral_constant<int, 0>{}) &&
+                     (k + 1 > TZ + 1 || step(k + 1, std::integral_constant<int, 1>{}));
+        }
     }
-    fwait<0>();
+    if (!ok && tid == 0) {
+        // a wait gave up: report it, and let every bulk copy this CTA issued and did not see
+        // land (groups g_done + 1 .. g_issued, at most NS of them, distinct slots) land,
+        // bounded, before the CTA's shared memory is released
+        atomicExch(fa.err, 4);
+        for (int g = g_done + 1; g <= g_issued; ++g)
+            fused_mbar_wait(full0 + 8u * (uint32_t)(g % NS), (uint32_t)((g / NS) & 1), fa.timeout_ns);
+    }
 }
 
 // Balanced tiling.  The CTA computes the first sublattice on NA = 256 / W4 rows,
@@ -353,12 +422,15 @@ __global__ void __launch_bounds__(256, MINB)
     fwait<0>();
 }
 
-// depth: copy groups in flight (2 or 3; 0 = 2), plus 8 for the balanced tiling
+// depth: copy groups in flight, 1..3 (0 = 2), plus 8 for the balanced tiling (2 or 3 there).
 bool fused_config_valid(int L, int TZ, int depth)
 {
     const int d = depth & ~8;
-    return L >= 256 && L <= 2048 && L % 256 == 0 && (L & (L - 1)) == 0 && TZ >= 1 && L % TZ == 0 &&
-           (d == 0 || d == 2 || d == 3) && (depth & ~11) == 0;
+    const bool bal = depth & 8;
+    if (!(L >= 256 && L <= 2048 && L % 256 == 0 && (L & (L - 1)) == 0 && TZ >= 1 && L % TZ == 0)) return false;
+    if ((depth & ~11) != 0) return false;
+    if (bal) return d == 0 || d == 2 || d == 3;
+    return d <= 3;
 }
 
 template <int RULE, int W4, int NS>
@@ -379,72 +451,109 @@ static cudaError_t fused_bal_rule(const uint32_t *cur, uint32_t *nxt, int L, int
     return cudaGetLastError();
 }
 
+// Round keys of Philox key S on the host (the key words plus i Weyl increments).
+static PhiloxKeys host_round_keys(uint64_t S)
+{
+    PhiloxKeys k;
+    uint32_t a = (uint32_t)S, b = (uint32_t)(S >> 32);
+    for (int i = 0; i < 10; ++i) {
+        k.k0[i] = a;
+        k.k1[i] = b;
+        a += 0x9E3779B9u;
+        b += 0xBB67AE85u;
+    }
+    return k;
+}
+
+// One launch per replica: its round keys and first sublattice travel as kernel parameters.
 template <int RULE, int W4, int NS>
 static cudaError_t fused_rule(const uint32_t *cur, uint32_t *nxt, int L, int R, uint64_t seed, int mixed, uint32_t t,
-                              int TZ, cudaStream_t s)
+                              int TZ, int *err, uint64_t timeout_ns, cudaStream_t s)
 {
+    constexpr int MINB = NS <= 4 ? 4 : 3;  // shared memory of four CTAs per SM for four slots
     constexpr size_t smem = fused_smem_bytes<W4, NS>();
-    cudaError_t e =
-        cudaFuncSetAttribute(k_mcs_fused<RULE, W4, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)  // shared memory for 3 CTAs per SM (the rest stays L1)
-        e = cudaFuncSetAttribute(k_mcs_fused<RULE, W4, NS>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                 cudaSharedmemCarveoutMaxShared);
+    auto kern = k_mcs_fused<RULE, W4, NS, MINB>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     const Geom g = make_geom(L);
     constexpr int TY = 256 / W4;
-    const dim3 grid((unsigned)((L / TY) * (L / TZ)), (unsigned)R);
-    k_mcs_fused<RULE, W4, NS><<<grid, 256, smem, s>>>(cur, nxt, g, mixed, t, seed, TZ);
+    const dim3 grid((unsigned)((L / TY) * (L / TZ)));
+    for (int r = 0; r < R; ++r) {
+        const uint64_t S = seed + (uint64_t)r;
+        FusedArgs a;
+        a.keys = host_round_keys(S);
+        a.A = mixed ? (uint32_t)mixed_first(S, t) : 0u;
+        a.Acur = reinterpret_cast<const uint4 *>(cur + (2 * (int64_t)r + a.A) * g.nw);
+        a.Bcur = reinterpret_cast<const uint4 *>(cur + (2 * (int64_t)r + 1 - a.A) * g.nw);
+        a.Anxt = reinterpret_cast<uint4 *>(nxt + (2 * (int64_t)r + a.A) * g.nw);
+        a.Bnxt = reinterpret_cast<uint4 *>(nxt + (2 * (int64_t)r + 1 - a.A) * g.nw);
+        a.L = L;
+        a.TZ = TZ;
+        a.t = t;
+        a.err = err;
+        a.timeout_ns = timeout_ns;
+        kern<<<grid, 256, smem, s>>>(a);
+    }
     return cudaGetLastError();
 }
 
 template <int RULE, int NS, bool BAL>
 static cudaError_t fused_one(const uint32_t *cur, uint32_t *nxt, int L, int R, uint64_t seed, int mixed, uint32_t t,
-                             int TZ, cudaStream_t s)
+                             int TZ, int *err, uint64_t timeout_ns, cudaStream_t s)
 {
     switch (L / 256) {
     case 1: return BAL ? fused_bal_rule<RULE, 1, NS>(cur, nxt, L, R, seed, mixed, t, TZ, s)
-                       : fused_rule<RULE, 1, NS>(cur, nxt, L, R, seed, mixed, t, TZ, s);
+                       : fused_rule<RULE, 1, NS>(cur, nxt, L, R, seed, mixed, t, TZ, err, timeout_ns, s);
     case 2: return BAL ? fused_bal_rule<RULE, 2, NS>(cur, nxt, L, R, seed, mixed, t, TZ, s)
-                       : fused_rule<RULE, 2, NS>(cur, nxt, L, R, seed, mixed, t, TZ, s);
+                       : fused_rule<RULE, 2, NS>(cur, nxt, L, R, seed, mixed, t, TZ, err, timeout_ns, s);
     case 4: return BAL ? fused_bal_rule<RULE, 4, NS>(cur, nxt, L, R, seed, mixed, t, TZ, s)
-                       : fused_rule<RULE, 4, NS>(cur, nxt, L, R, seed, mixed, t, TZ, s);
+                       : fused_rule<RULE, 4, NS>(cur, nxt, L, R, seed, mixed, t, TZ, err, timeout_ns, s);
     case 8: return BAL ? fused_bal_rule<RULE, 8, NS>(cur, nxt, L, R, seed, mixed, t, TZ, s)
-                       : fused_rule<RULE, 8, NS>(cur, nxt, L, R, seed, mixed, t, TZ, s);
+                       : fused_rule<RULE, 8, NS>(cur, nxt, L, R, seed, mixed, t, TZ, err, timeout_ns, s);
     default: return cudaErrorInvalidValue;
     }
 }
 
-// depth = copy groups in flight while a step computes: 2 (five slots) or 3 (six); +8: the
-// balanced tiling
+// depth = copy groups in flight while a step computes: 1..3 (four to six slots; 0 = 2); +8:
+// the balanced tiling (2: five slots, 3: six)
 template <int RULE>
 static cudaError_t fused_depth(const uint32_t *cur, uint32_t *nxt, int L, int R, uint64_t seed, int mixed,
-                               uint32_t t, int TZ, int depth, cudaStream_t s)
+                               uint32_t t, int TZ, int depth, int *err, uint64_t timeout_ns, cudaStream_t s)
 {
     switch (depth) {
-    case 3: return fused_one<RULE, 6, false>(cur, nxt, L, R, seed, mixed, t, TZ, s);
+    case 1: return fused_one<RULE, 4, false>(cur, nxt, L, R, seed, mixed, t, TZ, err, timeout_ns, s);
+    case 3: return fused_one<RULE, 6, false>(cur, nxt, L, R, seed, mixed, t, TZ, err, timeout_ns, s);
     case 8:
-    case 10: return fused_one<RULE, 5, true>(cur, nxt, L, R, seed, mixed, t, TZ, s);
-    case 11: return fused_one<RULE, 6, true>(cur, nxt, L, R, seed, mixed, t, TZ, s);
-    default: return fused_one<RULE, 5, false>(cur, nxt, L, R, seed, mixed, t, TZ, s);
+    case 10: return fused_one<RULE, 5, true>(cur, nxt, L, R, seed, mixed, t, TZ, err, timeout_ns, s);
+    case 11: return fused_one<RULE, 6, true>(cur, nxt, L, R, seed, mixed, t, TZ, err, timeout_ns, s);
+    default: return fused_one<RULE, 5, false>(cur, nxt, L, R, seed, mixed, t, TZ, err, timeout_ns, s);
     }
 }
 
 cudaError_t launch_sweeps_fused(uint32_t **cur, uint32_t **nxt, int L, int R, uint64_t seed, int rule, int64_t t0,
-                                int64_t n_mcs, int cycle, int TZ, int depth, cudaStream_t s, int64_t *launches)
+                                int64_t n_mcs, int cycle, int TZ, int depth, int *err, double timeout_s,
+                                cudaStream_t s, int64_t *launches)
 {
+    const uint64_t timeout_ns = (uint64_t)(timeout_s * 1e9);
     for (int64_t k = 0; k < n_mcs; ++k) {
         const uint32_t t = (uint32_t)(t0 + k);
         cudaError_t e;
         switch (rule) {
-        case TIE_GLAUBER: e = fused_depth<TIE_GLAUBER>(*cur, *nxt, L, R, seed, cycle, t, TZ, depth, s); break;
-        case TIE_ALWAYS: e = fused_depth<TIE_ALWAYS>(*cur, *nxt, L, R, seed, cycle, t, TZ, depth, s); break;
-        default: e = fused_depth<TIE_NEVER>(*cur, *nxt, L, R, seed, cycle, t, TZ, depth, s); break;
+        case TIE_GLAUBER:
+            e = fused_depth<TIE_GLAUBER>(*cur, *nxt, L, R, seed, cycle, t, TZ, depth, err, timeout_ns, s);
+            break;
+        case TIE_ALWAYS:
+            e = fused_depth<TIE_ALWAYS>(*cur, *nxt, L, R, seed, cycle, t, TZ, depth, err, timeout_ns, s);
+            break;
+        default: e = fused_depth<TIE_NEVER>(*cur, *nxt, L, R, seed, cycle, t, TZ, depth, err, timeout_ns, s); break;
         }
         if (e != cudaSuccess) return e;
         uint32_t *tmp = *cur;  // the new sweep becomes the current store
         *cur = *nxt;
         *nxt = tmp;
-        if (launches) ++*launches;
+        if (launches) *launches += (depth & 8) ? 1 : R;
     }
     return cudaSuccess;
 }

@@ -112,8 +112,9 @@ def test_zfuse_rules_and_replicas_L256(ising):
     for rule in (1, 2):
         _compare(ising, 256, 1, 17, [1, 3], rule=rule, variant=ising.VARIANT_ZFUSE, tile_z=32)
     _compare(ising, 256, 3, 22, [3], variant=ising.VARIANT_ZFUSE, tile_z=8)
-    # three copy groups in flight
+    # three copy groups in flight, and one (four slots, four CTAs per SM)
     _compare(ising, 256, 2, 23, [1, 4], variant=ising.VARIANT_ZFUSE, tile_z=16, depth=3)
+    _compare(ising, 256, 2, 24, [1, 4], variant=ising.VARIANT_ZFUSE, tile_z=2, depth=1)
 
 
 def test_zmarch_rules_L256(ising):
@@ -150,7 +151,7 @@ def test_variants_and_tiles_bit_identical(ising, L):
             assert np.array_equal(got[0], ref[0]), ("zdeep", tz, d)
             assert np.array_equal(grec, rec)
     for tz in (1, 16, 64, L):
-        for d in (0, 11):  # ragged tiles of 256 / W4 - 2 rows in the balanced form
+        for d in (0, 1, 3, 11):  # ragged tiles of 256 / W4 - 2 rows in the balanced form
             got, grec = _packed_state(ising, L, 1, 9, 6, variant=ising.VARIANT_ZFUSE, tile_z=tz, depth=d)
             assert np.array_equal(got[0], ref[0]), ("zfuse", tz, d)
             assert np.array_equal(grec, rec)
@@ -339,3 +340,21 @@ def test_tensor_core_wait_times_out_instead_of_hanging(ising):
     with ising.Ising(512, replicas=1, seed=2, corr=ising.CORR_TENSOR) as q:
         q.sweep(2)
         assert np.array_equal(q.measure(), good)
+
+
+@pytest.mark.parametrize("rule", RULES)
+def test_plain16_vs_oracle_ragged_rows(ising, rule):
+    # L = 192: 12 sixteen-byte chunks per row, so rows straddle warps and the Philox groups
+    # of a row (96 compressed indices) straddle rows; L = 16: one chunk per row
+    _compare(ising, 192, 1, 17, [1, 2, 5], rule=rule, form=ising.FORM_PLAIN)
+    _compare(ising, 16, 2, 3, [1, 4, 30], rule=rule, form=ising.FORM_PLAIN)
+
+
+@pytest.mark.parametrize("L", [512, 1024])
+def test_plain_and_packed_forms_identical_large(ising, L):
+    # rows of 32 and 64 chunks: warps inside rows; both cycles
+    for cycle in (ising.CYCLE_01, ising.CYCLE_MIXED):
+        a, ra = _packed_state(ising, L, 1, 9, 5, form=ising.FORM_PACKED, cycle=cycle)
+        b, rb = _packed_state(ising, L, 1, 9, 5, form=ising.FORM_PLAIN, cycle=cycle)
+        assert np.array_equal(a[0], b[0]), cycle
+        assert np.array_equal(ra, rb), cycle
