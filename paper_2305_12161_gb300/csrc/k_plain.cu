@@ -7,6 +7,8 @@
 // sublattice q, x = 2k + p): lane b owns site k = 32*kw + b (or b < L/2 for L < 64).
 // Byte loads of a warp span 64 consecutive bytes of a row; the warp's random word is one
 // Philox call shared by its lanes.
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -117,26 +119,31 @@ template <int RULE>
 __global__ void __launch_bounds__(256) k_sweep_plain16(int8_t *P, int L, int q, uint32_t t, uint64_t S)
 {
     constexpr uint32_t FULL = 0xffffffffu, M2 = 0x02020202u, B7 = 0x80808080u;
-    const int W = L >> 4;  // chunks per row
-    const int64_t nch = (int64_t)L * L * W;
+    const int W = L >> 4;                 // chunks per row (<= 256)
+    const int rpc = 256 / W;              // rows of a CTA pass
+    const int tr = (int)threadIdx.x / W;  // this thread's row in the pass, and its chunk
+    const int cx = (int)threadIdx.x - tr * W;
     const int lane = threadIdx.x & 31;
     const int64_t plane = (int64_t)L * L;
-    // nch is a multiple of 256 (L >= 16), and so are the grid and its stride: whole warps
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nch; c += (int64_t)gridDim.x * blockDim.x) {
-        // c < L^3 / 16 <= 2^32 for L <= 4096: 32-bit divisions
-        const uint32_t row = (uint32_t)c / (uint32_t)W;
-        const int cx = (int)((uint32_t)c - row * (uint32_t)W);
-        const int z = (int)(row / (uint32_t)L), y = (int)(row - (uint32_t)z * (uint32_t)L);
+    const int z = blockIdx.y;             // one plane per grid row: no division in the loop
+    const int64_t dzm = (z == 0 ? L - 1 : -1) * plane, dzp = (z == L - 1 ? 1 - L : 1) * plane;
+    // the pass loop is uniform over the CTA, so whole warps meet at the shuffles; threads past
+    // the pass's rows (W not a power of two) or past the plane compute on row L - 1 and store
+    // nothing
+    for (int yb = blockIdx.x * rpc; yb < L; yb += gridDim.x * rpc) {
+        const bool valid = tr < rpc && yb + tr < L;
+        const int y = valid ? yb + tr : L - 1;
+        const uint32_t row = (uint32_t)z * (uint32_t)L + (uint32_t)y;
         const int64_t base = (int64_t)row * L;  // first byte of the row
         const int64_t o = base + 16 * cx;
         const int64_t dym = (y == 0 ? L - 1 : -1) * (int64_t)L, dyp = (y == L - 1 ? 1 - L : 1) * (int64_t)L;
-        const int64_t dzm = (z == 0 ? L - 1 : -1) * plane, dzp = (z == L - 1 ? 1 - L : 1) * plane;
         const uint4 v = *reinterpret_cast<const uint4 *>(P + o);
         const uint4 ym = *reinterpret_cast<const uint4 *>(P + o + dym);
         const uint4 yp = *reinterpret_cast<const uint4 *>(P + o + dyp);
         const uint4 zm = *reinterpret_cast<const uint4 *>(P + o + dzm);
         const uint4 zp = *reinterpret_cast<const uint4 *>(P + o + dzp);
-        // x edges: byte x0 - 1 (top byte of the left chunk) and byte x0 + 16 (low byte of the right)
+        // x edges: byte x0 - 1 (top byte of the left chunk) and byte x0 + 16 (low byte of the
+        // right); lanes hold consecutive chunks of a row
         uint32_t left = __shfl_up_sync(FULL, v.w, 1);
         uint32_t right = __shfl_down_sync(FULL, v.x, 1);
         if (lane == 0 || cx == 0) left = (uint32_t)(uint8_t)P[base + (cx == 0 ? L - 1 : 16 * cx - 1)] << 24;
@@ -184,7 +191,7 @@ __global__ void __launch_bounds__(256) k_sweep_plain16(int8_t *P, int L, int q, 
             out[k] = (nd >> 7) * 0xFEu + 0x01010101u;
             changed |= out[k] != w[k];
         }
-        if (changed) *reinterpret_cast<uint4 *>(P + o) = make_uint4(out[0], out[1], out[2], out[3]);
+        if (changed && valid) *reinterpret_cast<uint4 *>(P + o) = make_uint4(out[0], out[1], out[2], out[3]);
     }
 }
 
@@ -195,10 +202,10 @@ static void sweeps_plain_rule(int8_t *plain, const Geom &g, int R, uint64_t seed
     const int64_t N = (int64_t)g.L * g.L * g.L;
     int64_t blocks = (g.nw + 7) / 8;
     if (blocks > (int64_t)device_sms() * 64) blocks = (int64_t)device_sms() * 64;
-    // 16 bytes per thread: L^3 / 16 threads in blocks of 256 (8 resident per SM)
-    int64_t blocks16 = N / 16 / 256;
-    if (blocks16 > (int64_t)device_sms() * 8 * 16) blocks16 = (int64_t)device_sms() * 8 * 16;
-    if (blocks16 < 1) blocks16 = 1;
+    // 16 bytes per thread: one grid row per plane, each CTA about eight passes of 256 / (L/16)
+    // rows along y
+    const int rpc = g.L >= 16 ? 256 / (g.L / 16) : 1;
+    const dim3 grid16((unsigned)std::max(1, (g.L / rpc + 7) / 8), (unsigned)g.L);
     for (int64_t k = 0; k < n; ++k) {
         const uint32_t t = (uint32_t)(t0 + k);
         for (int h = 0; h < 2; ++h)
@@ -206,7 +213,7 @@ static void sweeps_plain_rule(int8_t *plain, const Geom &g, int R, uint64_t seed
                 const uint64_t S = seed + (uint64_t)r;
                 const int q = cycle ? (mixed_first(S, t) ^ h) : h;
                 if (g.L % 16 == 0)
-                    k_sweep_plain16<RULE><<<(unsigned)blocks16, 256, 0, s>>>(plain + (int64_t)r * N, g.L, q, t, S);
+                    k_sweep_plain16<RULE><<<grid16, 256, 0, s>>>(plain + (int64_t)r * N, g.L, q, t, S);
                 else
                     k_sweep_plain<RULE><<<(unsigned)blocks, 256, 0, s>>>(plain + (int64_t)r * N, g, q, t, S);
             }
