@@ -222,6 +222,8 @@ def run_batched(torch, ising, inputs, K: int = 20, window: int = 20) -> dict:
         for c in ctxs:
             c.destroy()
     out["batched_vs_plain"] = out["batched_window_updates_per_ns"] / out["plain_window_updates_per_ns"]
+    out["batched_vs_packed_per_class"] = (out["batched_window_updates_per_ns"]
+                                          / out["packed_per_class_window_updates_per_ns"])
     return out
 
 
