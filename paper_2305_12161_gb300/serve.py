@@ -47,12 +47,13 @@ class Result:
         return self.finished_s - self.request.arrival_s
 
 
-def footprint_bytes(L: int, replicas: int, K: int) -> int:
+def footprint_bytes(L: int, replicas: int, K: int, **opts) -> int:
     """Device memory a request holds while it runs: its context as the library accounts it
-    (ising_footprint_bytes: packed lattices, records and, for L >= 512, the tensor-core
-    correlation scratch of L^3 bytes) plus the server's own result buffers for K
-    measured times (records and derived values of every replica)."""
-    ctx = ising.ising_footprint_bytes(L, replicas)
+    (ising_footprint_bytes: packed lattices, twice for the fused whole-sweep kernel, records
+    and, for L >= 512, the tensor-core correlation scratch of L^3 bytes) plus the server's
+    own result buffers for K measured times (records and derived values of every replica).
+    `opts`: the context options the request runs with (sweep kernel and tiling)."""
+    ctx = ising.ising_footprint_bytes(L, replicas, **opts)
     if ctx < 0:
         raise ValueError(f"no context for L={L}, replicas={replicas}")
     return ctx + K * replicas * (ising.ising_record_len(L) * 8 + 4 * 8)
@@ -80,11 +81,12 @@ def schedule_for(req: Request) -> list[int]:
 
 
 class _Active:
-    def __init__(self, req: Request, now: float, torch):
+    def __init__(self, req: Request, now: float, torch, opts=None):
         self.req = req
         self.times = schedule_for(req)
         self.stream = torch.cuda.Stream()
-        self.ctx = ising.Ising(req.L, replicas=req.replicas, seed=req.seed, stream=self.stream)
+        self.opts = dict(opts or {})
+        self.ctx = ising.Ising(req.L, replicas=req.replicas, seed=req.seed, stream=self.stream, **self.opts)
         K = len(self.times)
         self.rec = torch.empty((K, req.replicas, self.ctx.record_len), dtype=torch.int64, device="cuda")
         self.der = torch.empty((K, req.replicas, 4), dtype=torch.float64, device="cuda")
@@ -98,10 +100,17 @@ class _Active:
 
 
 class QuenchServer:
+    """`tune`: pick each lattice size's sweep kernel and tiling with the library's autotuner
+    the first time a request of that size is submitted (every choice gives the same results;
+    the fused whole-sweep kernel, which the tuner picks for the larger sizes, holds a second
+    packed store, which the admission footprint counts)."""
+
     def __init__(self, budget_bytes: float = 150e9, max_slots: int = 16, quantum_mcs: int = 64,
-                 max_inflight: int = 2, c: float = 0.5):
+                 max_inflight: int = 2, c: float = 0.5, tune: bool = True):
         import torch
         self.torch = torch
+        self.tune = tune
+        self.opts: dict[int, dict] = {}  # L -> context options
         self.budget = float(budget_bytes)
         self.max_slots = max_slots
         self.quantum = quantum_mcs
@@ -117,16 +126,29 @@ class QuenchServer:
     def now(self) -> float:
         return time.perf_counter() - self.t0
 
+    def options_for(self, L: int) -> dict:
+        """Context options of requests of size L (autotuned once per size when `tune`)."""
+        if L not in self.opts:
+            o = {}
+            if self.tune:
+                t = ising.ising_tune_sweep(L, 1, probe_mcs=4)
+                o = {k: t[k] for k in ("variant", "tile_y", "tile_z", "depth")}
+            self.opts[L] = o
+        return self.opts[L]
+
+    def footprint(self, req: Request) -> int:
+        return footprint_bytes(req.L, req.replicas, req.K, **self.options_for(req.L))
+
     def submit(self, req: Request) -> None:
-        if footprint_bytes(req.L, req.replicas, req.K) > self.budget:
+        if self.footprint(req) > self.budget:
             raise ValueError(f"request {req.id} needs more than the whole HBM budget")
         self.pending.append(req)
 
     def _admit(self) -> None:
         admitted, self.pending, self.used = admit(self.pending, len(self.active), self.used, self.budget,
-                                                  self.max_slots, lambda r: footprint_bytes(r.L, r.replicas, r.K))
+                                                  self.max_slots, self.footprint)
         for req in admitted:
-            self.active.append(_Active(req, self.now(), self.torch))
+            self.active.append(_Active(req, self.now(), self.torch, self.options_for(req.L)))
 
     def _issue(self, a: _Active) -> None:
         # one quantum: sweep towards the next measured time, measure when it is reached
@@ -152,14 +174,17 @@ class QuenchServer:
                 der = a.der.cpu().numpy()
                 self.results.append(Result(a.req, a.times, rec, der, a.admitted_s, self.now()))
                 self.updates += a.updates
-                self.used -= footprint_bytes(a.req.L, a.req.replicas, a.req.K)
+                self.used -= self.footprint(a.req)
                 a.ctx.destroy()
             else:
                 still.append(a)
         self.active = still
 
     def run(self, trace: list[Request], idle_sleep_s: float = 0.0005) -> list[Result]:
-        """Serve `trace` (arrival_s relative to the start) until every request is done."""
+        """Serve `trace` (arrival_s relative to the start) until every request is done.  The
+        sizes in the trace are tuned before the clock starts."""
+        for r in trace:
+            self.options_for(r.L)
         self.t0 = time.perf_counter()
         queue = sorted(trace, key=lambda r: r.arrival_s)
         i = 0
@@ -191,11 +216,12 @@ def trace_requests(n: int, seed: int = 0, rate_hz: float = 20.0, K: int = 12, **
             for d in inputs.serving_trace(n, seed=seed, rate_hz=rate_hz, **kw)]
 
 
-def run_alone(req: Request, c: float = 0.5) -> Result:
-    """The same request served by itself (reference for the mix)."""
+def run_alone(req: Request, c: float = 0.5, opts=None) -> Result:
+    """The same request served by itself (reference for the mix), with the default sweep
+    kernel unless `opts` names one."""
     import torch
     t0 = time.perf_counter()
-    a = _Active(req, 0.0, torch)
+    a = _Active(req, 0.0, torch, opts)
     for k, tk in enumerate(a.times):
         a.ctx.sweep(tk - a.ctx.t)
         a.ctx.measure_device(a.rec[k], a.der[k], c=c)
