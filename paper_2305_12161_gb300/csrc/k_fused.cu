@@ -16,6 +16,8 @@
 // N/4 bytes, against 3 N/8 for two half-sweeps.  The planes of the tile stream into shared
 // memory by TMA bulk copies (cp.async.bulk, one per contiguous run of rows) issued by one
 // thread and completing on mbarriers; every wait is bounded in wall time.
+#include <algorithm>
+#include <cstdlib>
 #include <type_traits>
 
 #include "common.cuh"
@@ -91,7 +93,7 @@ struct FusedArgs {
     PhiloxKeys keys;           // round keys of the replica's Philox key (seed + replica)
     const uint4 *Acur, *Bcur;  // store of sweep t: first-updated sublattice A and the other, B
     uint4 *Anxt, *Bnxt;        // store of sweep t + 1
-    int L, TZ;
+    int L, nzb;                // z-blocks: block b holds planes b L / nzb .. (b + 1) L / nzb - 1
     uint32_t t, A;             // sweep index, first sublattice (its tie-bit phase)
     int *err;                  // set to 4 when a bounded wait gave up
     uint64_t timeout_ns;
@@ -144,12 +146,14 @@ __global__ void __launch_bounds__(256, MINB) k_mcs_fused(const __grid_constant__
     uint4 *ring = fsm;                   // [NS][SLOT], group g in slot g % NS
     uint4 *anew = fsm + NS * SLOT;       // [3][NEW], plane zA in slot k % 3
     uint64_t *full = reinterpret_cast<uint64_t *>(anew + 3 * NEW);  // [NS]
-    const int L = fa.L, TZ = fa.TZ;
+    const int L = fa.L;
     const int tid = threadIdx.x;
     const int nty = (L + TYO - 1) / TYO;
     const int y0 = (int)(blockIdx.x % nty) * TYO;  // even: TYO is even
     const int nown = min(TYO, L - y0);
-    const int z0 = (int)(blockIdx.x / nty) * TZ;
+    const int zb = (int)(blockIdx.x / nty);
+    const int z0 = (int)((int64_t)zb * L / fa.nzb);
+    const int TZ = (int)((int64_t)(zb + 1) * L / fa.nzb) - z0;  // planes of this CTA's tile
     const int32_t plane4 = L * W4;
     const int32_t vol4 = L * plane4;
     auto wrapL = [&](int a) { return a < 0 ? a + L : (a >= L ? a - L : a); };
@@ -293,11 +297,33 @@ __global__ void __launch_bounds__(256, MINB) k_mcs_fused(const __grid_constant__
     }
 }
 
-// depth: copy groups in flight, 1..3 (0 = 2), plus 8 for the balanced tiling.
+// depth: copy groups in flight, 1..3 (0 = 2), plus 8 for the balanced tiling, plus 16 for
+// z-blocks fitted to the resident CTAs (see fitted_zblocks).
 bool fused_config_valid(int L, int TZ, int depth)
 {
     return L >= 256 && L <= 2048 && L % 256 == 0 && (L & (L - 1)) == 0 && TZ >= 1 && L % TZ == 0 &&
-           (depth & ~11) == 0;
+           (depth & ~27) == 0;
+}
+
+// Number of z-blocks near L / TZ (within 25%) whose tile count nty * nzb fills the last wave
+// of `slots` resident CTAs best (ties: the one nearest L / TZ).  Blocks then hold L / nzb
+// planes, rounded per block: tiles of one launch differ by at most one plane, and the
+// launch's last wave is nearly full instead of leaving SMs idle.
+static int fitted_zblocks(int L, int TZ, int nty, int slots)
+{
+    const int nom = L / TZ;
+    int best = nom;
+    double best_eff = -1.0;
+    for (int c = std::max(1, (3 * nom) / 4); c <= std::min(L / 2, (5 * nom + 3) / 4); ++c) {
+        const int64_t ctas = (int64_t)nty * c;
+        const int64_t waves = (ctas + slots - 1) / slots;
+        const double eff = (double)ctas / (double)(waves * slots);
+        if (eff > best_eff + 1e-9 || (eff > best_eff - 1e-9 && std::abs(c - nom) < std::abs(best - nom))) {
+            best_eff = eff;
+            best = c;
+        }
+    }
+    return best;
 }
 
 // Round keys of Philox key S on the host (the key words plus i Weyl increments).
@@ -317,7 +343,7 @@ static PhiloxKeys host_round_keys(uint64_t S)
 // One launch per replica: its round keys and first sublattice travel as kernel parameters.
 template <int RULE, int W4, int NS, bool BAL>
 static cudaError_t fused_rule(const uint32_t *cur, uint32_t *nxt, int L, int R, uint64_t seed, int mixed, uint32_t t,
-                              int TZ, int *err, uint64_t timeout_ns, cudaStream_t s)
+                              int TZ, bool fit, int *err, uint64_t timeout_ns, cudaStream_t s)
 {
     constexpr size_t smem = fused_smem_bytes<W4, NS, BAL>();
     // CTAs per SM that the shared memory allows (228 KB per SM, 1 KB reserved per CTA); the
@@ -330,7 +356,15 @@ static cudaError_t fused_rule(const uint32_t *cur, uint32_t *nxt, int L, int R, 
     if (e != cudaSuccess) return e;
     const Geom g = make_geom(L);
     constexpr int TYO = FusedTile<W4, BAL>::TYO;
-    const dim3 grid((unsigned)(((L + TYO - 1) / TYO) * (L / TZ)));
+    const int nty = (L + TYO - 1) / TYO;
+    int nzb = L / TZ;
+    if (fit) {
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
+        if (e != cudaSuccess) return e;
+        nzb = fitted_zblocks(L, TZ, nty, std::max(1, per_sm) * device_sms());
+    }
+    const dim3 grid((unsigned)(nty * nzb));
     for (int r = 0; r < R; ++r) {
         const uint64_t S = seed + (uint64_t)r;
         FusedArgs a;
@@ -341,7 +375,7 @@ static cudaError_t fused_rule(const uint32_t *cur, uint32_t *nxt, int L, int R, 
         a.Anxt = reinterpret_cast<uint4 *>(nxt + (2 * (int64_t)r + a.A) * g.nw);
         a.Bnxt = reinterpret_cast<uint4 *>(nxt + (2 * (int64_t)r + 1 - a.A) * g.nw);
         a.L = L;
-        a.TZ = TZ;
+        a.nzb = nzb;
         a.t = t;
         a.err = err;
         a.timeout_ns = timeout_ns;
@@ -352,31 +386,32 @@ static cudaError_t fused_rule(const uint32_t *cur, uint32_t *nxt, int L, int R, 
 
 template <int RULE, int NS, bool BAL>
 static cudaError_t fused_one(const uint32_t *cur, uint32_t *nxt, int L, int R, uint64_t seed, int mixed, uint32_t t,
-                             int TZ, int *err, uint64_t timeout_ns, cudaStream_t s)
+                             int TZ, bool fit, int *err, uint64_t timeout_ns, cudaStream_t s)
 {
     switch (L / 256) {
-    case 1: return fused_rule<RULE, 1, NS, BAL>(cur, nxt, L, R, seed, mixed, t, TZ, err, timeout_ns, s);
-    case 2: return fused_rule<RULE, 2, NS, BAL>(cur, nxt, L, R, seed, mixed, t, TZ, err, timeout_ns, s);
-    case 4: return fused_rule<RULE, 4, NS, BAL>(cur, nxt, L, R, seed, mixed, t, TZ, err, timeout_ns, s);
-    case 8: return fused_rule<RULE, 8, NS, BAL>(cur, nxt, L, R, seed, mixed, t, TZ, err, timeout_ns, s);
+    case 1: return fused_rule<RULE, 1, NS, BAL>(cur, nxt, L, R, seed, mixed, t, TZ, fit, err, timeout_ns, s);
+    case 2: return fused_rule<RULE, 2, NS, BAL>(cur, nxt, L, R, seed, mixed, t, TZ, fit, err, timeout_ns, s);
+    case 4: return fused_rule<RULE, 4, NS, BAL>(cur, nxt, L, R, seed, mixed, t, TZ, fit, err, timeout_ns, s);
+    case 8: return fused_rule<RULE, 8, NS, BAL>(cur, nxt, L, R, seed, mixed, t, TZ, fit, err, timeout_ns, s);
     default: return cudaErrorInvalidValue;
     }
 }
 
 // depth = copy groups in flight while a step computes: 1..3 (four to six slots; 0 = 2); +8:
-// the balanced tiling
+// the balanced tiling; +16: z-blocks fitted to the resident CTAs
 template <int RULE>
 static cudaError_t fused_depth(const uint32_t *cur, uint32_t *nxt, int L, int R, uint64_t seed, int mixed,
                                uint32_t t, int TZ, int depth, int *err, uint64_t timeout_ns, cudaStream_t s)
 {
-    switch (depth) {
-    case 1: return fused_one<RULE, 4, false>(cur, nxt, L, R, seed, mixed, t, TZ, err, timeout_ns, s);
-    case 3: return fused_one<RULE, 6, false>(cur, nxt, L, R, seed, mixed, t, TZ, err, timeout_ns, s);
-    case 9: return fused_one<RULE, 4, true>(cur, nxt, L, R, seed, mixed, t, TZ, err, timeout_ns, s);
+    const bool fit = depth & 16;
+    switch (depth & ~16) {
+    case 1: return fused_one<RULE, 4, false>(cur, nxt, L, R, seed, mixed, t, TZ, fit, err, timeout_ns, s);
+    case 3: return fused_one<RULE, 6, false>(cur, nxt, L, R, seed, mixed, t, TZ, fit, err, timeout_ns, s);
+    case 9: return fused_one<RULE, 4, true>(cur, nxt, L, R, seed, mixed, t, TZ, fit, err, timeout_ns, s);
     case 8:
-    case 10: return fused_one<RULE, 5, true>(cur, nxt, L, R, seed, mixed, t, TZ, err, timeout_ns, s);
-    case 11: return fused_one<RULE, 6, true>(cur, nxt, L, R, seed, mixed, t, TZ, err, timeout_ns, s);
-    default: return fused_one<RULE, 5, false>(cur, nxt, L, R, seed, mixed, t, TZ, err, timeout_ns, s);
+    case 10: return fused_one<RULE, 5, true>(cur, nxt, L, R, seed, mixed, t, TZ, fit, err, timeout_ns, s);
+    case 11: return fused_one<RULE, 6, true>(cur, nxt, L, R, seed, mixed, t, TZ, fit, err, timeout_ns, s);
+    default: return fused_one<RULE, 5, false>(cur, nxt, L, R, seed, mixed, t, TZ, fit, err, timeout_ns, s);
     }
 }
 

@@ -35,7 +35,9 @@ SweepConfig default_sweep_config(int L, int R);
 // pointers, so after n sweeps *cur holds the state.  Both stores hold 2*R*nw words.
 // depth: copy groups in flight while a step computes, 1..3 (0 = 2; SweepConfig.depth); +8 selects
 // the balanced tiling (tiles of 256/(L/256) - 2 rows, the halo rows computed by ordinary threads;
-// 2 or 3 groups).  The first tiling launches once per replica and bounds its waits for copies by
+// 2 or 3 groups); +16 fits the number of z-blocks (tiles of nearly equal depth, within 25% of
+// tile_z) to the resident CTAs so that the launch's last wave is nearly full.  The kernel
+// launches once per replica and bounds its waits for copies by
 // timeout_s of wall time; one that gives up sets *err = 4 (the sweep's results are then invalid).
 bool fused_config_valid(int L, int tile_z, int depth);
 cudaError_t launch_sweeps_fused(uint32_t **cur, uint32_t **nxt, int L, int R, uint64_t seed, int rule, int64_t t0,

@@ -37,7 +37,7 @@ def test_menger_start_and_quench(ising, L, k, form):
 
 
 @pytest.mark.parametrize("variant,L,depth", [(1, 16, 0), (1, 64, 0), (3, 256, 0), (4, 256, 0), (2, 256, 0),
-                                             (5, 256, 0), (5, 256, 11), (5, 256, 1), (5, 256, 9), (5, 512, 11)])
+                                             (5, 256, 0), (5, 256, 11), (5, 256, 1), (5, 256, 9), (5, 512, 11), (5, 512, 27)])
 def test_mixed_cycle_vs_oracle(ising, variant, L, depth):
     R, seed = 3, 21
     with ising.Ising(L, replicas=R, seed=seed, variant=variant, depth=depth, cycle=ising.CYCLE_MIXED) as q:

@@ -107,6 +107,9 @@ def test_zfuse_balanced_L256_vs_oracle(ising, tz):
     _compare(ising, 256, 1, 18, [1, 2, 5], variant=ising.VARIANT_ZFUSE, tile_z=tz, depth=11)
     _compare(ising, 256, 2, 19, [3], rule=1, variant=ising.VARIANT_ZFUSE, tile_z=tz, depth=8)
     _compare(ising, 256, 1, 20, [2, 3], rule=2, variant=ising.VARIANT_ZFUSE, tile_z=tz, depth=9)
+    # z-blocks fitted to the resident CTAs (tiles of unequal depth)
+    _compare(ising, 256, 1, 21, [1, 2, 5], variant=ising.VARIANT_ZFUSE, tile_z=tz, depth=27)
+    _compare(ising, 256, 2, 22, [3], rule=1, variant=ising.VARIANT_ZFUSE, tile_z=tz, depth=19)
 
 
 def test_zfuse_rules_and_replicas_L256(ising):
@@ -152,7 +155,7 @@ def test_variants_and_tiles_bit_identical(ising, L):
             assert np.array_equal(got[0], ref[0]), ("zdeep", tz, d)
             assert np.array_equal(grec, rec)
     for tz in (1, 16, 64, L):
-        for d in (0, 1, 3, 9, 11):  # ragged tiles of 256 / W4 - 2 rows in the balanced form
+        for d in (0, 1, 3, 9, 11, 19, 25, 27):  # ragged tiles of 256 / W4 - 2 rows in the balanced form
             got, grec = _packed_state(ising, L, 1, 9, 6, variant=ising.VARIANT_ZFUSE, tile_z=tz, depth=d)
             assert np.array_equal(got[0], ref[0]), ("zfuse", tz, d)
             assert np.array_equal(grec, rec)
