@@ -724,7 +724,7 @@ int ising_tune_sweep(int L, int replicas, int probe_mcs, const ising_opts *base,
             }
         }
         for (int tz : {16, 32, 64, 128})
-            for (int mb : {1, 2, 3, 9, 10, 11, 19, 25, 27}) {
+            for (int mb : {1, 2, 3, 9, 10, 11, 19, 25, 26, 27}) {
                 const SweepConfig cf{VARIANT_ZFUSE, 256 / W4, tz, mb};
                 if (sweep_config_valid(L, cf)) cands.push_back(cf);
             }

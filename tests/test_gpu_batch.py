@@ -149,3 +149,37 @@ def test_missing_group_member_times_out_instead_of_hanging(ising):
     with ising.Ising(64, replicas=1, seed=1) as q:
         q.sweep(2)
         q.measure()
+
+
+def test_config4_mix_in_the_bench_configuration(ising):
+    # the mixed batch of the benchmark (512 x 64^3 + 64 x 128^3 + 16 x 256^3 + 4 x 512^3, one
+    # seed per lattice), tuned work list, 10^4 MCS with 20 log-spaced measurements as one graph:
+    # the first and last lattice of every class against a single context measured at the same
+    # times (every recorded time), the oracle's recount of their final states, and a one-MCS
+    # oracle advance of the final state of one lattice per class
+    from paper_2305_12161_gb300 import inputs
+    classes = [(64, 512, 1), (128, 64, 513), (256, 16, 577), (512, 4, 593)]
+    times = inputs.log_schedule(10_000, 20)
+    with ising.Batch(classes) as b:
+        b.tune(probe_mcs=4)
+        b.reinit()
+        rec, der = b.run(times, c=0.5)
+        assert b.t == times[-1]
+        finals = {}
+        for ci, (L, R, seed) in enumerate(classes):
+            for r in (0, R - 1):
+                with ising.Ising(L, replicas=1, seed=seed + r) as q:
+                    t = 0
+                    for k, tk in enumerate(times):
+                        q.sweep(tk - t)
+                        t = tk
+                        assert np.array_equal(b.record_of(rec[k], ci, r), q.measure()[0]), (L, r, tk)
+                    finals[(ci, r)] = q.get_spins(0)
+                assert np.array_equal(oracle.record(finals[(ci, r)], times[-1]), b.record_of(rec[-1], ci, r)), (L, r)
+        b.sweep(1)
+        for ci, (L, R, seed) in enumerate(classes):
+            s = finals[(ci, 0)]
+            oracle.sweeps(s, times[-1], 1, seed)
+            with ising.Ising(L, replicas=1, seed=seed) as q:
+                q.set_spins(s, 0)
+                assert np.array_equal(b.get_packed(ci, 0), q.get_packed(0)), L
