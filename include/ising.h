@@ -144,7 +144,8 @@ int ising_create(ising_ctx **out, int L, int replicas, uint64_t seed);
 int ising_create_ex(ising_ctx **out, int L, int replicas, uint64_t seed, const ising_opts *opts);
 
 /* Device bytes that a context of `replicas` lattices of size L with options *opts (NULL:
- * defaults) holds once it has measured: the packed store (2 x L^3/16 bytes per replica,
+ * defaults) holds once it has measured (no counterpart in the paper: it serves admission by
+ * device footprint, e.g. the serving loop's): the packed store (2 x L^3/16 bytes per replica,
  * twice for the fused whole-sweep kernel, variant 5), the byte-per-spin lattice of the
  * PLAIN form (L^3 per replica), the records and derived values, and the tensor-core
  * correlation scratch (L^3 bytes, allocated by the first measurement whose method is the

@@ -3,7 +3,8 @@
 // sweep t (`cur`) and writes the store of sweep t+1 (`nxt`), so no CTA ever reads a value
 // that another CTA of the same launch has already replaced.
 //
-// A CTA owns a tile of full rows and TZ planes and marches along z.  With A the sublattice
+// A CTA owns a tile of full rows and TZ planes (a z-block: the blocks of a launch hold
+// L / nzb planes each, rounded per block) and marches along z.  With A the sublattice
 // updated first and B the other, step k updates A on plane zA = z0 - 1 + k for the tile's
 // rows and one halo row on each side, then B on plane zB = zA - 1 for the tile's rows; B's
 // neighbours are A's new values of planes zB - 1 .. zB + 1, which this CTA has just
@@ -48,9 +49,6 @@ __device__ __forceinline__ uint4 xshift(const uint4 &C, uint32_t edge_left_w, ui
 
 }  // namespace
 
-// Bounded wait on phase `parity` of an mbarrier: spins on try_wait until the phase has
-// completed or timeout_ns of %globaltimer have passed (with a cap on rounds as a backstop);
-// false when it gave up.
 __device__ __forceinline__ uint64_t fused_timer_ns()
 {
     uint64_t t;
@@ -58,6 +56,9 @@ __device__ __forceinline__ uint64_t fused_timer_ns()
     return t;
 }
 
+// Bounded wait on phase `parity` of an mbarrier: spins on try_wait until the phase has
+// completed or timeout_ns of %globaltimer have passed (with a cap on rounds as a backstop);
+// false when it gave up.
 __device__ __forceinline__ bool fused_mbar_wait(uint32_t addr, uint32_t parity, uint64_t timeout_ns)
 {
     uint32_t done = 0;
@@ -136,7 +137,7 @@ template <int RULE, int W4, int NS, int MINB, bool BAL>
 __global__ void __launch_bounds__(256, MINB) k_mcs_fused(const __grid_constant__ FusedArgs fa)
 {
     using T = FusedTile<W4, BAL>;
-    constexpr int NT = 256, RW = 32 / W4;
+    constexpr int RW = 32 / W4;
     constexpr int NR = T::NR, TYO = T::TYO, RA = T::RA, RB = T::RB, SLOT = T::SLOT;
     constexpr int NB = RB * W4;                // B items of a slot (A items follow)
     constexpr int NEW = RA * W4;               // items of a new-A slot
