@@ -82,8 +82,10 @@ typedef struct {
                        (z-marching specialised on the row width) fixes it to 256/(L/256) */
     int tile_z;     /* packed z-marching variants: planes per tile (0 = automatic) */
     int depth;      /* variant 4: planes in flight in the copy pipeline, 2..4 (0 = 3);
-                       variant 5: copy groups in flight, 2 or 3 (0 = 2), plus 8 for tiles of
-                       256/(L/256) - 2 rows whose halo rows are computed by ordinary threads */
+                       variant 5: copy groups in flight, 1..3 (0 = 2), plus 8 for tiles of
+                       256/(L/256) - 2 rows whose halo rows are computed by ordinary threads,
+                       plus 16 for z-blocks fitted to the CTAs resident on the device (tile_z
+                       is then their nominal depth); any other value is ISING_EINVAL */
     int cycle;      /* ising_cycle: sublattice order of each sweep */
     int corr;       /* ising_corr: how the correlation sums D_a(r) are computed */
     int scheme;     /* ising_scheme: checkerboard or double checkerboard */
