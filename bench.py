@@ -161,9 +161,11 @@ BATCH_CLASSES = [(64, 512, 1), (128, 64, 513), (256, 16, 577), (512, 4, 593)]  #
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of a sweep kernel, from
 # one ncu capture each (the file under profiles/ gives the command); (kernel, L) -> (bytes, source)
-TRAFFIC_NCU = {("k_sweep_zfast", 2048): (1.596e9, "ncu, profiles/k_sweep_zfast_L2048.md"),
-               ("k_mcs_fused", 2048): (2.158e9, "ncu, profiles/k_mcs_fused_L2048.md (balanced tiling, z-blocks fitted "
-                                                "near 64 planes, six slots; other configurations: not captured)")}
+# DRAM bytes per launch from one ncu capture of the kernel as built, by (kernel, L, tile_z,
+# depth); other configurations were not captured and report null
+TRAFFIC_NCU = {("k_sweep_zfast", 2048, 32, 0): (1.596e9, "ncu, profiles/k_sweep_zfast_L2048.md"),
+               ("k_mcs_fused", 2048, 64, 26): (2.163e9, "ncu, profiles/k_mcs_fused_L2048.md (balanced tiling, "
+                                                        "z-blocks fitted near 64 planes, five slots)")}
 
 
 def run_batched(torch, ising, inputs, K: int = 20, window: int = 20) -> dict:
@@ -689,9 +691,7 @@ def main():
     # DRAM bytes per launch are not measured here (that needs a profiler): they are quoted
     # from the ncu capture of the same kernel at L=2048 named in traffic_src, and only for
     # the kernel that capture measured
-    traffic, traffic_src = TRAFFIC_NCU.get((kname, L), (None, None))
-    if kname == "k_mcs_fused" and (tuned["tile_z"], tuned["depth"]) != (64, 27):
-        traffic, traffic_src = None, None  # the capture measured another configuration
+    traffic, traffic_src = TRAFFIC_NCU.get((kname, L, tuned["tile_z"], tuned["depth"]), (None, None))
     roof_sweep = {"kernel": kname + (" (whole sweep)" if fused else " (half-sweep)"), "bound": "hbm",
                   "achieved": sweep_gbs,
                   "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": sweep_gbs / pk["hbm_gbs"], "traffic": traffic,

@@ -135,6 +135,55 @@ __device__ __forceinline__ U4 philox4x32_10_rk(uint32_t c0, uint32_t c1, uint32_
     return U4{c0, c1, c2, c3};
 }
 
+// Philox4x32-10 of the counter (c0, t, q, 0) for many c0 under one key, with what depends on
+// t, q and the key alone worked out once (philox_lead): in round 1 the product of q and words
+// 0 and 1, in round 2 the product of round 1's word 0, in round 3 word 3.  The output is
+// philox4x32_10(c0, t, q, 0, key); a draw takes 36 multiplies instead of 40.
+struct PhiloxLead {
+    uint32_t x0_2;  // round 2: word 0 = mulhi(M1, word 2) ^ x0_2
+    uint32_t x2_2;  // round 2: word 2 = word 3 ^ x2_2
+    uint32_t x2_3;  // round 3: word 2 = mulhi(M0, word 0) ^ x2_3
+};
+
+__host__ __device__ inline PhiloxLead philox_lead(uint32_t t, uint32_t q, const PhiloxKeys &k)
+{
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint64_t p1 = (uint64_t)M1 * q;
+    const uint32_t w0 = (uint32_t)(p1 >> 32) ^ t ^ k.k0[0], w1 = (uint32_t)p1;  // round 1, words 0 and 1
+    const uint64_t p0 = (uint64_t)M0 * w0;                                       // round 2's product of word 0
+    PhiloxLead ld;
+    ld.x0_2 = w1 ^ k.k0[1];
+    ld.x2_2 = (uint32_t)(p0 >> 32) ^ k.k1[1];
+    ld.x2_3 = (uint32_t)p0 ^ k.k1[2];  // round 2's word 3 meets round 3's key word
+    return ld;
+}
+
+__host__ __device__ __forceinline__ U4 philox4x32_10_lead(uint32_t c0, const PhiloxLead &ld, const PhiloxKeys &k)
+{
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    uint32_t h0, l0, h1, l1;
+    mul_hi_lo(M0, c0, h0, l0);  // round 1: words 2 and 3
+    const uint32_t a2 = h0 ^ k.k1[0], a3 = l0;
+    mul_hi_lo(M1, a2, h1, l1);  // round 2: words 0, 1, 2 (word 3 is a constant)
+    const uint32_t b0 = h1 ^ ld.x0_2, b1 = l1, b2 = a3 ^ ld.x2_2;
+    mul_hi_lo(M0, b0, h0, l0);  // round 3
+    mul_hi_lo(M1, b2, h1, l1);
+    c0 = h1 ^ b1 ^ k.k0[2];
+    uint32_t c1 = l1, c2 = h0 ^ ld.x2_3, c3 = l0;
+#pragma unroll
+    for (int i = 3; i < 10; ++i) {
+        mul_hi_lo(M0, c0, h0, l0);
+        mul_hi_lo(M1, c2, h1, l1);
+        const uint32_t n0 = h1 ^ c1 ^ k.k0[i];
+        const uint32_t n2 = h0 ^ c3 ^ k.k1[i];
+        c0 = n0;
+        c1 = l1;
+        c2 = n2;
+        c3 = l0;
+    }
+    return U4{c0, c1, c2, c3};
+}
+
 __host__ __device__ __forceinline__ uint32_t pick(const U4 &o, int i)
 {
     return i == 0 ? o.x : (i == 1 ? o.y : (i == 2 ? o.z : o.w));
