@@ -707,7 +707,7 @@ def main():
         gram_flops = 3 * (nbt * (nbt + 1) // 2) * 2 * 128 * 128 * L * L
         fp8_peak = 2 * pk["bf16_tflops_sustained"]
         gram_tflops = gram_flops / meas_avg_s / 1e12
-        roof_corr = {"kernel": "measurement: 3 x (e4m3 expansion + k_gram_tma) + k_mb", "bound": "tensor",
+        roof_corr = {"kernel": "measurement: k_expand_x_e4m3 + 3 x k_gram_tma (helper warps expand y, z) + k_mb4", "bound": "tensor",
                      "achieved": gram_tflops, "peak": fp8_peak, "unit": "TFLOP/s (fp8)",
                      "frac": gram_tflops / fp8_peak, "traffic": None, "peak_src": pk["src"] + " bf16 sustained x 2",
                      "avg_launch_ms": meas_avg_s * 1e3, "flops_per_launch": gram_flops}

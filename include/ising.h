@@ -99,8 +99,8 @@ typedef struct {
  * matrix of the L positions over the L^2 lines of the axis, computed on the 5th-generation
  * tensor cores (tcgen05.mma, e4m3 operands loaded by TMA, fp32 accumulators in tensor memory;
  * exact: |G| <= L^2 <= 2^24); L a multiple of 128 in 256..2048; it allocates a scratch of
- * L^3 bytes (one axis of one replica expanded to e4m3: 8.6 GB at L=2048) at its first use and
- * keeps it (ising_release_scratch frees it).  AUTO:
+ * 2 L^3 bytes (two axes of one replica expanded to e4m3, one multiplied while the next is
+ * expanded: 17.2 GB at L=2048) at its first use and keeps it (ising_release_scratch frees it).  AUTO:
  * TENSOR for L >= 512 where it is supported and its scratch can be allocated (measured on
  * GB300: 1.9x faster than POPCOUNT at L=512, 3.5x at L=2048; slower at L=256), else POPCOUNT. */
 typedef enum { ISING_CORR_AUTO = 0, ISING_CORR_POPCOUNT = 1, ISING_CORR_TENSOR = 2 } ising_corr;
@@ -150,7 +150,7 @@ int ising_create_ex(ising_ctx **out, int L, int replicas, uint64_t seed, const i
  * device footprint, e.g. the serving loop's): the packed store (2 x L^3/16 bytes per replica,
  * twice for the fused whole-sweep kernel, variant 5), the byte-per-spin lattice of the
  * PLAIN form (L^3 per replica), the records and derived values, and the tensor-core
- * correlation scratch (L^3 bytes, allocated by the first measurement whose method is the
+ * correlation scratch (2 L^3 bytes, allocated by the first measurement whose method is the
  * tensor-core path: ISING_CORR_TENSOR, or AUTO with L >= 512).  Pure host arithmetic,
  * no device is touched; what ising_create_ex allocates comes from the same accounting.
  * Not included: buffers that only the optional calls allocate while they run or keep

@@ -10,10 +10,11 @@
 //
 // Only the upper block triangle of G is computed (G is symmetric); an entry of an
 // off-diagonal tile stands for both ordered pairs (j, k) and (k, j).  Per replica and axis:
-// the axis's lines are expanded once into e4m3 rows (k_expand_e4m3), and k_gram_tma
-// accumulates the 128 x 128 tiles of G by tcgen05.mma in tensor memory from TMA-loaded,
-// 128-byte swizzled shared-memory operands; each entry's -G/2 is added to D at its cyclic
-// distance; the records start from N/2.
+// the axis's lines are expanded once into e4m3 rows in one of two scratch halves (x by
+// k_expand_x_e4m3; y and z by the helper warps of the previous axis's product, into the
+// other half), and k_gram_tma accumulates the 128 x 128 tiles of G by tcgen05.mma in tensor
+// memory from TMA-loaded, 128-byte swizzled shared-memory operands; each entry's -G/2 is
+// added to D at its cyclic distance; the records start from N/2.
 #include <cuda.h>
 
 #include <algorithm>
@@ -29,6 +30,7 @@ constexpr int GT_STAGES = 4;     // TMA pipeline depth (48 KB per stage)
 constexpr int GT_KB = 128;       // K bytes (= lines) per stage and operand box
 constexpr int GT_STAGE_BYTES = (TM_T + GT_N) * GT_KB;
 constexpr int UMMA_WAIT_LIMIT = 1 << 30;  // backstop on try_wait rounds (the wall-time bound comes first)
+constexpr int GT_THREADS = 256;  // Gram CTA: warps 0-3 load, multiply and read back; 4-7 expand the next axis
 
 
 // Four e4m3 values from the four bits of n (n < 16): bit i -> byte i, +1.0 (0x38) when
@@ -108,6 +110,16 @@ __device__ __forceinline__ void store_e4m3_word(uint8_t *dst, uint32_t v)
     reinterpret_cast<uint4 *>(dst)[1] = hi;
 }
 
+// The same with streaming stores (evict first), for the helper warps of a Gram launch: the
+// operands of the running product stay in L2.
+__device__ __forceinline__ void store_e4m3_word_cs(uint8_t *dst, uint32_t v)
+{
+    uint4 lo, hi;
+    expand_e4m3_word(v, lo, hi);
+    __stcs(reinterpret_cast<uint4 *>(dst), lo);
+    __stcs(reinterpret_cast<uint4 *>(dst) + 1, hi);
+}
+
 // x axis, straight from the packed store: a CTA stages both sublattices' words of 128
 // consecutive rows (row = y + L z; four bundles B of 32 rows) in shared memory with coalesced
 // loads; a warp then takes word column kw of both parity classes pi of those rows (lane = row
@@ -179,23 +191,60 @@ __global__ void __launch_bounds__(256) k_expand_x_e4m3(const uint32_t *S0, const
     }
 }
 
-// y and z axes: blockIdx.y steps over positions p, the threads over the columns
-// cc = (pi L + a) W + kw of that position (consecutive words of one lattice row), so no 64-bit
-// division per word.
-__global__ void k_expand_e4m3(const uint32_t *S0, const uint32_t *S1, Geom g, int axis, uint8_t *E)
+// y and z axes, one packed word each: column cc = (pi L + a) W + kw of position p (consecutive
+// words of one lattice row), the 32 lines 32 cc .. 32 cc + 31.
+__device__ __forceinline__ void expand_yz_word(const uint32_t *S0, const uint32_t *S1, const Geom &g, int axis,
+                                               uint8_t *E, int p, int cc)
 {
     const int L = g.L, W = g.W;
-    const int ncols = (int)((int64_t)L * L / 32);
     const int64_t blk = (int64_t)L * GT_KB;  // bytes of one 128-line chunk of all positions
-    for (int p = blockIdx.y; p < L; p += gridDim.y) {
-        for (int cc = blockIdx.x * blockDim.x + threadIdx.x; cc < ncols; cc += gridDim.x * blockDim.x) {
-            const int kw = cc % W;
-            const int rest = cc / W;  // pi L + a
-            const int a = rest % L, pi = rest / L;
-            const int y = axis == 1 ? p : a, z = axis == 1 ? a : p;
-            const uint32_t v = __ldg((((pi + y + z) & 1) ? S1 : S0) + ((int64_t)z * L + y) * W + kw);
-            store_e4m3_word(E + (int64_t)(cc >> 2) * blk + (int64_t)p * GT_KB + 32 * (cc & 3), v);
+    const int kw = cc % W;
+    const int rest = cc / W;  // pi L + a
+    const int a = rest % L, pi = rest / L;
+    const int y = axis == 1 ? p : a, z = axis == 1 ? a : p;
+    const uint32_t v = __ldg((((pi + y + z) & 1) ? S1 : S0) + ((int64_t)z * L + y) * W + kw);
+    store_e4m3_word(E + (int64_t)(cc >> 2) * blk + (int64_t)p * GT_KB + 32 * (cc & 3), v);
+}
+
+// The expansion a Gram launch's helper warps run for the next product: axis `axis` (1: y,
+// 2: z) of the lattice (S0, S1) into E (nullptr: none).  (The x axis, bit-transposed, has a
+// kernel of its own: run by the helper warps it slowed the product it shared the SMs with by
+// more than its own 2.3 ms at L = 2048.)
+struct ExpandJob {
+    const uint32_t *S0, *S1;
+    uint8_t *E;
+    int axis;
+};
+
+// Helper thread h of nh: its share of job j.
+__device__ __forceinline__ void run_expand_job(const ExpandJob &j, const Geom &g, int h, int nh)
+{
+    if (!j.E) return;
+    // words i = h + nh (U m + u): the U loads of a round are issued before its stores
+    constexpr int U = 16;
+    const int L = g.L, W = g.W;
+    const uint32_t ncols = (uint32_t)((int64_t)L * L / 32), total = (uint32_t)L * ncols;  // L^3 / 32 < 2^31
+    const int64_t blk = (int64_t)L * GT_KB;
+    for (uint32_t i0 = (uint32_t)h; i0 < total; i0 += (uint32_t)nh * U) {
+        uint32_t v[U];
+        uint8_t *dst[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint32_t i = i0 + (uint32_t)nh * u;
+            v[u] = 0;
+            dst[u] = nullptr;
+            if (i < total) {
+                const int p = (int)(i / ncols), cc = (int)(i - (uint32_t)p * ncols);
+                const int kw = cc % W, rest = cc / W;  // rest = pi L + a
+                const int a = rest % L, pi = rest / L;
+                const int y = j.axis == 1 ? p : a, z = j.axis == 1 ? a : p;
+                v[u] = __ldg((((pi + y + z) & 1) ? j.S1 : j.S0) + ((int64_t)z * L + y) * W + kw);
+                dst[u] = j.E + (int64_t)(cc >> 2) * blk + (int64_t)p * GT_KB + 32 * (cc & 3);
+            }
         }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (dst[u]) store_e4m3_word_cs(dst[u], v[u]);
     }
 }
 
@@ -215,10 +264,14 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *tm,
 // 0 loads the 128 x 128-byte box of tile bj and the 256 x 128-byte box of the super-tile by TMA
 // (128-byte swizzle) into a ring of GT_STAGES stages, thread 32 issues four tcgen05.mma of
 // 128 x 256 x 32 per stage into a 256-column fp32 accumulator in tensor memory and frees the
-// stage by tcgen05.commit; then all four warps read the accumulator and add each entry of an
+// stage by tcgen05.commit; then warps 0-3 read the accumulator and add each entry of an
 // upper-triangle tile (bk >= bj, bk < nb) as -G/2 to D at its cyclic distance.  The CTAs of
 // one K slice run together and stream the same columns, so L2 serves the tiles' repeated
-// reads.
+// reads.  Warps 4-7 meanwhile expand the next product's axis (`next`) into the other scratch
+// half; they wait on nothing and join the CTA at the barrier after the main loop.  Measured:
+// L=1024 a whole measurement 2.18 ms against 2.93 with every expansion a kernel of its own;
+// L=2048 21.1 against 21.5 ms (there the helpers' 8.6 GB of stores cost the product part of
+// its L2 hits).
 //
 // Every wait is bounded (timeout_ns of %globaltimer).  A wait that gives up clears the CTA's
 // `flag`, sets *err and the CTA stops without adding anything to D.  Before it leaves:
@@ -231,10 +284,10 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *tm,
 //    the dealloc rather than free tensor memory the tensor core may still write.
 // No test provokes these paths; the stall test drops stage 0's loads of CTA 0 before any
 // load or MMA is in flight.
-__global__ void __launch_bounds__(128, 1) k_gram_tma(const __grid_constant__ CUtensorMap tmA,
-                                                     const __grid_constant__ CUtensorMap tmB, int L, int nb,
-                                                     int nunits, int split, int64_t *D, int *err,
-                                                     uint64_t timeout_ns, int inject)
+__global__ void __launch_bounds__(GT_THREADS, 1) k_gram_tma(const __grid_constant__ CUtensorMap tmA,
+                                                            const __grid_constant__ CUtensorMap tmB, int L, int nb,
+                                                            int nunits, int split, int64_t *D, int *err,
+                                                            uint64_t timeout_ns, int inject, ExpandJob next)
 {
     extern __shared__ __align__(1024) uint8_t gsm[];
     uint8_t *stage0 = gsm;  // [S][A 16 KB, B 32 KB]
@@ -263,7 +316,7 @@ __global__ void __launch_bounds__(128, 1) k_gram_tma(const __grid_constant__ CUt
     const int c0 = (int)((int64_t)nk * sl / split), c1 = (int)((int64_t)nk * (sl + 1) / split);
     const int n = c1 - c0;
 
-    for (int i = tid; i <= H; i += 128) sacc[i] = 0;
+    for (int i = tid; i <= H; i += GT_THREADS) sacc[i] = 0;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
                      "r"(GT_N));
@@ -286,7 +339,10 @@ __global__ void __launch_bounds__(128, 1) k_gram_tma(const __grid_constant__ CUt
     const uint32_t tmem = *tmem_holder;
 
     int prod_end = 0;  // producer: stages [0, prod_end) were armed (expect_tx) and loaded
-    if (tid == 0) {  // producer
+    if (warp >= 4) {  // helper warps: the next product's expansion, into the other scratch half
+        run_expand_job(next, make_geom(L), (int)(blockIdx.x * (GT_THREADS - 128) + tid - 128),
+                       (int)(gridDim.x * (GT_THREADS - 128)));
+    } else if (tid == 0) {  // producer
         for (int t = 0; t < n; ++t) {
             const int st = t % GT_STAGES;
             if (t >= GT_STAGES &&
@@ -347,7 +403,7 @@ __global__ void __launch_bounds__(128, 1) k_gram_tma(const __grid_constant__ CUt
     }
     __syncthreads();
     const bool ok = *flag && n > 0;
-    if (ok) {
+    if (ok && warp < 4) {  // warp w reads tensor-memory lanes 32 w .. 32 w + 31
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const int j = j0 + 32 * warp + lane;  // this thread's row of the tile (TMEM lane)
 #pragma unroll 1
@@ -385,7 +441,7 @@ __global__ void __launch_bounds__(128, 1) k_gram_tma(const __grid_constant__ CUt
     if (warp == 0 && !*mma_pending)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(GT_N));
     if (!ok) return;
-    for (int i = 1 + tid; i <= H; i += 128)
+    for (int i = 1 + tid; i <= H; i += GT_THREADS)
         if (sacc[i]) atomicAdd((unsigned long long *)(D + i), (unsigned long long)(-(sacc[i] / 2)));
 }
 
@@ -416,8 +472,8 @@ bool corr_mma_supported(int L) { return L >= 256 && L <= 2048 && L % TM_T == 0 &
 
 size_t corr_mma_scratch_bytes(int L, int R)
 {
-    (void)R;  // replicas are multiplied one after the other through one expanded axis
-    return (size_t)L * L * L;
+    (void)R;  // replicas are multiplied one after the other through two expanded axes
+    return (size_t)2 * L * L * L;
 }
 
 cudaError_t launch_corr_mma(const uint32_t *lat, int L, int R, int64_t *rec, uint32_t *scratch, int *err,
@@ -425,22 +481,25 @@ cudaError_t launch_corr_mma(const uint32_t *lat, int L, int R, int64_t *rec, uin
 {
     const uint64_t timeout_ns = (uint64_t)(timeout_s * 1e9);
     const Geom g = make_geom(L);
-    uint8_t *E = reinterpret_cast<uint8_t *>(scratch);
+    // two halves of L^3 bytes: product i reads half i % 2 while its helper warps expand product
+    // i + 1 into the other
+    uint8_t *E[2] = {reinterpret_cast<uint8_t *>(scratch), reinterpret_cast<uint8_t *>(scratch) + (size_t)L * L * L};
     EncodeTiledFn enc = encode_tiled();
     if (!enc) return cudaErrorNotSupported;
     // E viewed as rows of 128 bytes: row (chunk * L + position); boxes of 128 and 256 rows
-    CUtensorMap tmA, tmB;
+    CUtensorMap tmA[2], tmB[2];
     const cuuint64_t gdim[2] = {(cuuint64_t)GT_KB, (cuuint64_t)L * L * L / GT_KB};
     const cuuint64_t gstride[1] = {(cuuint64_t)GT_KB};
     const cuuint32_t boxA[2] = {GT_KB, TM_T}, boxB[2] = {GT_KB, GT_N};
     const cuuint32_t estr[2] = {1, 1};
-    if (enc(&tmA, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, E, gdim, gstride, boxA, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS ||
-        enc(&tmB, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, E, gdim, gstride, boxB, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-        return cudaErrorInvalidValue;
+    for (int h = 0; h < 2; ++h)
+        if (enc(&tmA[h], CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, E[h], gdim, gstride, boxA, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS ||
+            enc(&tmB[h], CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, E[h], gdim, gstride, boxB, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
@@ -454,29 +513,25 @@ cudaError_t launch_corr_mma(const uint32_t *lat, int L, int R, int64_t *rec, uin
     int split = sms / nunits;  // one CTA per SM: K slices x units <= SMs
     if (split < 1) split = 1;
     const int64_t H = L / 2, RL = 3 + 3 * (H + 1);
-    const int ncols_e = (int)((int64_t)L * L / 32);
     const size_t xsm = expand_x_smem_bytes(g.W);
     if ((e = cudaFuncSetAttribute(k_expand_x_e4m3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsm)) !=
         cudaSuccess)
         return e;
-    int64_t nl = 0;
+    // per replica: x expanded by its own kernel into half 0; its product's helper warps expand
+    // y into half 1, and the y product's helpers z into half 0; the z product runs alone
     for (int r = 0; r < R; ++r) {
-        const uint32_t *S0 = lat + 2 * (int64_t)r * g.nw;
+        const uint32_t *S0 = lat + 2 * (int64_t)r * g.nw, *S1 = S0 + g.nw;
+        k_expand_x_e4m3<<<(unsigned)std::min<int64_t>((int64_t)L * L / 128, (int64_t)sms * 2), 256, xsm, s>>>(
+            S0, S1, g, E[0]);
         for (int axis = 0; axis < 3; ++axis) {
-            if (axis == 0) {  // 32 x 32 bit transposes, one warp per word column (both parities)
-                k_expand_x_e4m3<<<(unsigned)std::min<int64_t>((int64_t)L * L / 128, (int64_t)sms * 2), 256, xsm, s>>>(
-                    S0, S0 + g.nw, g, E);
-            } else {          // positions over grid.y, columns over the threads
-                const dim3 eg((unsigned)std::max(1, std::min(8, ncols_e / 256)), (unsigned)L);
-                k_expand_e4m3<<<eg, 256, 0, s>>>(S0, S0 + g.nw, g, axis, E);
-            }
-            k_gram_tma<<<(unsigned)(nunits * split), 128, smem, s>>>(tmA, tmB, L, nb, nunits, split,
-                                                                     rec + r * RL + 3 + axis * (H + 1), err,
-                                                                     timeout_ns, inject && r == 0 && axis == 1);
-            nl += 2;
+            const ExpandJob next = axis < 2 ? ExpandJob{S0, S1, E[(axis + 1) % 2], axis + 1}
+                                            : ExpandJob{nullptr, nullptr, nullptr, 0};
+            k_gram_tma<<<(unsigned)(nunits * split), GT_THREADS, smem, s>>>(
+                tmA[axis % 2], tmB[axis % 2], L, nb, nunits, split, rec + r * RL + 3 + axis * (H + 1), err,
+                timeout_ns, inject && r == 0 && axis == 1, next);
         }
     }
-    if (launches) *launches += nl;
+    if (launches) *launches += 4 * (int64_t)R;
     return cudaGetLastError();
 }
 

@@ -50,7 +50,7 @@ class Result:
 def footprint_bytes(L: int, replicas: int, K: int, **opts) -> int:
     """Device memory a request holds while it runs: its context as the library accounts it
     (ising_footprint_bytes: packed lattices, twice for the fused whole-sweep kernel, records
-    and, for L >= 512, the tensor-core correlation scratch of L^3 bytes) plus the server's
+    and, for L >= 512, the tensor-core correlation scratch of 2 L^3 bytes) plus the server's
     own result buffers for K measured times (records and derived values of every replica).
     `opts`: the context options the request runs with (sweep kernel and tiling)."""
     ctx = ising.ising_footprint_bytes(L, replicas, **opts)

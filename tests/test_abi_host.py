@@ -127,7 +127,7 @@ def test_batch_create_rejects_bad_arguments(lib):
 
 def test_footprint_bytes_counts_every_buffer(lib):
     # packed store L^3/8 bytes per replica (1 bit per spin), records (3 + 3(L/2+1)) int64 and
-    # 4 doubles per replica, a 16-byte status word; the tensor-core correlation scratch L^3
+    # 4 doubles per replica, a 16-byte status word; the tensor-core correlation scratch 2 L^3
     # bytes for L >= 512 by default (not for the bit-count method), the fused kernel's second
     # store, and L^3 bytes per replica for the plain form
     from paper_2305_12161_gb300 import ising
@@ -136,7 +136,7 @@ def test_footprint_bytes_counts_every_buffer(lib):
         tensor = (L >= 512) if tensor is None else tensor
         rec = 8 * R * (3 + 3 * (L // 2 + 1)) + 32 * R + 16
         lat = R * (L**3 // 8 if L >= 64 else 8 * L * L)  # L < 64: one padded 32-bit word per row
-        return lat * (2 if fused else 1) + rec + (R * L**3 if plain else 0) + (L**3 if tensor else 0)
+        return lat * (2 if fused else 1) + rec + (R * L**3 if plain else 0) + (2 * L**3 if tensor else 0)
 
     for L, R in ((32, 1), (64, 16), (256, 8), (512, 1), (1024, 3), (2048, 1)):
         assert ising.ising_footprint_bytes(L, R) == expect(L, R), (L, R)

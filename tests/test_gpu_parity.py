@@ -155,7 +155,7 @@ def test_variants_and_tiles_bit_identical(ising, L):
             assert np.array_equal(got[0], ref[0]), ("zdeep", tz, d)
             assert np.array_equal(grec, rec)
     for tz in (1, 16, 64, L):
-        for d in (0, 1, 3, 9, 11, 19, 25, 27):  # ragged tiles of 256 / W4 - 2 rows in the balanced form
+        for d in (0, 1, 3, 9, 11, 19, 25, 26, 27):  # ragged tiles of 256 / W4 - 2 rows in the balanced form
             got, grec = _packed_state(ising, L, 1, 9, 6, variant=ising.VARIANT_ZFUSE, tile_z=tz, depth=d)
             assert np.array_equal(got[0], ref[0]), ("zfuse", tz, d)
             assert np.array_equal(grec, rec)
@@ -164,7 +164,7 @@ def test_variants_and_tiles_bit_identical(ising, L):
 @pytest.mark.parametrize("rule", RULES)
 def test_zfuse_matches_zfast_L512_rules_replicas_odd_count(ising, rule):
     ref, rec = _packed_state(ising, 512, 2, 31, 7, tie=rule, variant=ising.VARIANT_ZFAST)
-    for d in (0, 10):
+    for d in (0, 10, 26):
         got, grec = _packed_state(ising, 512, 2, 31, 7, tie=rule, variant=ising.VARIANT_ZFUSE, tile_z=32, depth=d)
         for r in range(2):
             assert np.array_equal(got[r], ref[r]), (r, d)

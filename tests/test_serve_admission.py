@@ -21,8 +21,8 @@ def test_footprint_includes_the_correlation_scratch():
         own = K * R * (ising.ising_record_len(L) * 8 + 32)
         assert fp == ising.ising_footprint_bytes(L, R) + own
         packed = R * L**3 // 8
-        if L >= 512:  # L^3 bytes of e4m3 operands once the first measurement runs
-            assert fp >= packed + L**3
+        if L >= 512:  # 2 L^3 bytes of e4m3 operands once the first measurement runs
+            assert fp >= packed + 2 * L**3
         else:
             assert fp < 2 * packed + own + 4096
     with pytest.raises(ValueError):
