@@ -167,6 +167,7 @@ static constexpr size_t fused_smem_bytes()
 template <int RULE, int W4, int NS, int MINB, bool BAL>
 __global__ void __launch_bounds__(256, MINB) k_mcs_fused(const __grid_constant__ FusedArgs fa)
 {
+    __shared__ int s_fail;  // set by a thread whose wait gave up, read by all after the step's barrier
     using T = FusedTile<W4, BAL>;
     constexpr int RW = 32 / W4;
     constexpr int NR = T::NR, TYO = T::TYO, RA = T::RA, RB = T::RB, SLOT = T::SLOT;
@@ -217,6 +218,7 @@ __global__ void __launch_bounds__(256, MINB) k_mcs_fused(const __grid_constant__
         if (g >= 2) copy_rows(dst + 16u * NB, fa.Acur + wrapL(z0 - 3 + g) * plane4, y0 - 1, RA, mbar);
     };
     if (tid == 0) {
+        s_fail = 0;
         for (int i = 0; i < NS; ++i)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(full0 + 8u * (uint32_t)i));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -261,7 +263,11 @@ __global__ void __launch_bounds__(256, MINB) k_mcs_fused(const __grid_constant__
         const int na0 = k % 3, na1 = (k + 2) % 3, na2 = (k + 1) % 3;
         bool fail = !fused_mbar_wait(full0 + 8u * (uint32_t)sl2, (uint32_t)((g2 / NS) & 1), fa.timeout_ns);
         if (!fail) g_done = g2;
-        if (__syncthreads_or(fail)) return false;
+        // a plain barrier and a flag in shared memory: the barrier with an OR reduction
+        // (__syncthreads_or) made the whole kernel 6% slower
+        if (fail) atomicOr(&s_fail, 1);
+        __syncthreads();
+        if (*(volatile int *)&s_fail) return false;
         if (tid == 0 && k >= 1) issue(k - 1 + NS);  // the slot of group k - 1, last read in step k - 1
         const uint4 *S0 = ring + sl0 * SLOT;  // B plane zA - 1
         const uint4 *S1 = ring + sl1 * SLOT;  // B plane zA
