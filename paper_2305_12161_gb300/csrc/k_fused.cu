@@ -167,7 +167,10 @@ static constexpr size_t fused_smem_bytes()
 template <int RULE, int W4, int NS, int MINB, bool BAL>
 __global__ void __launch_bounds__(256, MINB) k_mcs_fused(const __grid_constant__ FusedArgs fa)
 {
-    __shared__ int s_fail;  // set by a thread whose wait gave up, read by all after the step's barrier
+    // first step whose wait gave up in some thread (0x7fffffff: none); every thread reads it
+    // after the step's barrier and leaves when it is at or before its own step, so a failure
+    // posted during step k + 1 by a thread that ran ahead is not seen as one of step k
+    __shared__ int s_fail;
     using T = FusedTile<W4, BAL>;
     constexpr int RW = 32 / W4;
     constexpr int NR = T::NR, TYO = T::TYO, RA = T::RA, RB = T::RB, SLOT = T::SLOT;
@@ -218,7 +221,7 @@ __global__ void __launch_bounds__(256, MINB) k_mcs_fused(const __grid_constant__
         if (g >= 2) copy_rows(dst + 16u * NB, fa.Acur + wrapL(z0 - 3 + g) * plane4, y0 - 1, RA, mbar);
     };
     if (tid == 0) {
-        s_fail = 0;
+        s_fail = 0x7fffffff;
         for (int i = 0; i < NS; ++i)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(full0 + 8u * (uint32_t)i));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -265,9 +268,9 @@ __global__ void __launch_bounds__(256, MINB) k_mcs_fused(const __grid_constant__
         if (!fail) g_done = g2;
         // a plain barrier and a flag in shared memory: the barrier with an OR reduction
         // (__syncthreads_or) made the whole kernel 6% slower
-        if (fail) atomicOr(&s_fail, 1);
+        if (fail) atomicMin(&s_fail, k);
         __syncthreads();
-        if (*(volatile int *)&s_fail) return false;
+        if (*(volatile int *)&s_fail <= k) return false;
         if (tid == 0 && k >= 1) issue(k - 1 + NS);  // the slot of group k - 1, last read in step k - 1
         const uint4 *S0 = ring + sl0 * SLOT;  // B plane zA - 1
         const uint4 *S1 = ring + sl1 * SLOT;  // B plane zA
