@@ -195,6 +195,10 @@ def run_batched(torch, ising, inputs, K: int = 20, window: int = 20) -> dict:
         w = bt.tune(probe_mcs=4)
         out["autotuner_w_local"] = w
         out["plan"] = bt.plan()
+        kernels = [bt.class_config(ci) for ci in range(len(BATCH_CLASSES))]
+        out["class_kernels"] = {f"{L}^3": ("persistent" if k["variant"] < 0 else
+                                           f"variant {k['variant']}, tile_z {k['tile_z']}, depth {k['depth']}")
+                                for (L, _, _), k in zip(BATCH_CLASSES, kernels)}
         rec = torch.empty((K, bt.record_words), dtype=torch.int64, device="cuda")
         der = torch.empty((K, bt.lattices, 4), dtype=torch.float64, device="cuda")
         bt.reinit()
@@ -214,9 +218,15 @@ def run_batched(torch, ising, inputs, K: int = 20, window: int = 20) -> dict:
         bt.sync()
         out["window_mcs"] = window
         out["batched_window_updates_per_ns"] = window * spins / (ms_w * 1e-3) / 1e9
+    # the packed form per class runs every class on the kernel the batch gave it (the tuned
+    # single-lattice kernel of a streamed class; the default kernel of the others)
+    packed_kw = [dict(variant=k["variant"], tile_y=k["tile_y"], tile_z=k["tile_z"], depth=k["depth"])
+                 if k["variant"] > 0 else {} for k in kernels]
     for form, key in ((ising.FORM_PLAIN, "plain_window_updates_per_ns"),
                       (ising.FORM_PACKED, "packed_per_class_window_updates_per_ns")):
-        ctxs = [ising.Ising(L, replicas=R, seed=sd, form=form, stream=stream) for L, R, sd in BATCH_CLASSES]
+        ctxs = [ising.Ising(L, replicas=R, seed=sd, form=form, stream=stream,
+                            **(packed_kw[i] if form == ising.FORM_PACKED else {}))
+                for i, (L, R, sd) in enumerate(BATCH_CLASSES)]
         for c in ctxs:
             c.sweep(1)
         ms_p = timed(lambda: [c.sweep(window) for c in ctxs])

@@ -299,8 +299,9 @@ int64_t ising_launch_count(const ising_ctx *ctx);
  * and swept there; larger ones are split into slabs over a group of CTAs that meet at
  * a bounded barrier in global memory between half-sweeps.  Classes with L a multiple of
  * 256 and at least the streaming threshold (default 256; ising_batch_set_streamed) are
- * instead swept in the same segment by the single-lattice z-marching kernel, which
- * streams them faster than slab groups do.  Every lattice follows
+ * instead swept in the same segment by a single-lattice sweep kernel (the z-marching one
+ * by default, the one ising_batch_tune picks after tuning), which streams them faster
+ * than slab groups do.  Every lattice follows
  * exactly the trajectory of the single-lattice entry points (same rule, order and
  * random bits), so batching changes speed, not results.
  * Records and derived values are concatenated in class order, replica-major within a
@@ -333,14 +334,32 @@ int ising_batch_get_time(const ising_batch *b, int64_t *t);
 int ising_batch_plan(const ising_batch *b, int *ntasks, int *nlocal, int *ngroups, int *capacity);
 /* Autotuner: probe rounds of probe_mcs sweeps (they advance the batch) time every CTA,
  * set the relative cost of whole-lattice CTAs from the measured time per spin and
- * rebuild the work list; *w_local_out receives the chosen weight. */
+ * rebuild the work list; *w_local_out receives the chosen weight.  Then every streamed
+ * class, one after the other, keeps whichever of its default kernel and the kernel that
+ * ising_tune_sweep picks for its L and replica count alone gives the faster whole segment
+ * (the streamed classes of a segment run side by side on their own streams, forked from
+ * and joined back into the batch's stream, so they compete for the SMs). */
 int ising_batch_tune(ising_batch *b, int probe_mcs, double *w_local_out);
+/* Sweep kernel of streamed class `cls` (Methods, "Checkerboard update"; every choice gives
+ * the same trajectory): opts->variant, tile_y, tile_z and depth as for ising_create_ex,
+ * variant 0 = the default for the class's L and replica count; the other fields are
+ * ignored.  Variant 5 (both sublattices per launch, up to 16 replicas of the class per
+ * launch) allocates a second store of the class's size, kept until ising_batch_destroy;
+ * a segment then runs its whole sweeps in pairs between the two stores and an odd last
+ * sweep in place, so the state is always in the first store between segments.
+ * ISING_EINVAL: class out of range, not streamed, or a configuration not valid for its L;
+ * ISING_ENOMEM: the second store could not be allocated.  Drops the cached schedule graph.
+ * ising_batch_set_streamed puts every streamed class back on its default kernel. */
+int ising_batch_set_class_opts(ising_batch *b, int cls, const ising_opts *opts);
+/* The sweep kernel of class `cls` into opts (variant -1: the class is swept by the
+ * persistent kernel); ISING_EINVAL for a bad class or NULL pointer. */
+int ising_batch_get_class_opts(const ising_batch *b, int cls, ising_opts *opts);
 int ising_batch_set_weights(ising_batch *b, double w_local, double w_group);
-/* Classes with L >= min_L and L % 256 == 0 are swept by the z-marching kernel, the
+/* Classes with L >= min_L and L % 256 == 0 are swept by a single-lattice kernel, the
  * others by the persistent kernel; min_L <= 0 puts every class in the persistent kernel.
  * Rebuilds the work list (results are unchanged). */
 int ising_batch_set_streamed(ising_batch *b, int min_L);
-/* Number of classes currently swept by the z-marching kernel. */
+/* Number of classes currently swept by a single-lattice kernel. */
 int ising_batch_streamed_classes(const ising_batch *b);
 /* Failure injection for tests: CTA `cta` returns at once, so its slab group's barrier
  * waits run out after timeout_s; the segment then ends early and the next

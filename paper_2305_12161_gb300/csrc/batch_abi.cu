@@ -24,8 +24,9 @@ struct BatchClass {
     uint32_t *lat;       // R * 2 * nw words
     int64_t rec_off;     // offset of this class's records in a batch record block
     int64_t der_off;     // offset (in replicas) of this class's derived rows
-    int streamed;        // swept by the z-marching kernel instead of the persistent one
-    SweepConfig cfg;     // its kernel configuration
+    int streamed;        // swept by a single-lattice sweep kernel instead of the persistent one
+    SweepConfig cfg;     // that kernel's configuration (streamed classes)
+    uint32_t *alt;       // second store of the fused whole-sweep kernel (allocated when chosen)
 };
 
 bool packed_L_ok(int L) { return (L >= 64 && L % 64 == 0) || L == 4 || L == 8 || L == 16 || L == 32; }
@@ -36,6 +37,10 @@ struct ising_batch {
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    // streamed classes after the first run on side streams forked from and joined back into
+    // `stream` within each segment (ev[0]: fork, ev[1 + i]: join of side[i])
+    std::vector<cudaStream_t> side;
+    std::vector<cudaEvent_t> ev;
     int rule = 0;
     std::vector<BatchClass> cls;
     int64_t nlat = 0, rec_words = 0;
@@ -203,10 +208,38 @@ int enqueue_segment(ising_batch *b, int64_t n, unsigned long long *cta_ns)
                                 b->stream));
             b->launches += 1;
         }
-        for (const auto &k : b->cls)
-            if (k.streamed)
-                BCK(b, launch_sweeps_packed(k.lat, k.L, k.R, k.seed, b->rule, b->t, chunk, 0, k.cfg, b->stream,
+        // the streamed classes, each on its own stream: their short launches (a few
+        // microseconds of work each) overlap instead of waiting for one another
+        int nstreamed = 0, si = 0;
+        for (const auto &k : b->cls) nstreamed += k.streamed;
+        if (nstreamed > 1) BCK(b, cudaEventRecord(b->ev[0], b->stream));
+        for (const auto &k : b->cls) {
+            if (!k.streamed) continue;
+            cudaStream_t st = b->stream;
+            if (si > 0) {
+                st = b->side[si - 1];
+                BCK(b, cudaStreamWaitEvent(st, b->ev[0], 0));
+            }
+            if (k.cfg.variant == VARIANT_ZFUSE) {
+                // whole sweeps between the two stores: an even count ends in k.lat again, and
+                // an odd last sweep runs in place, so a segment always leaves the state there
+                const int even = chunk & ~1;
+                uint32_t *cur = k.lat, *nxt = k.alt;
+                if (even)
+                    BCK(b, launch_sweeps_fused(&cur, &nxt, k.L, k.R, k.seed, b->rule, b->t, even, 0, k.cfg.tile_z,
+                                               k.cfg.depth, b->d_status, (double)b->timeout_ns * 1e-9, st,
+                                               &b->launches));
+                if (chunk & 1)
+                    BCK(b, launch_sweeps_packed(k.lat, k.L, k.R, k.seed, b->rule, b->t + even, 1, 0,
+                                                default_sweep_config(k.L, k.R), st, &b->launches));
+            } else {
+                BCK(b, launch_sweeps_packed(k.lat, k.L, k.R, k.seed, b->rule, b->t, chunk, 0, k.cfg, st,
                                             &b->launches));
+            }
+            if (si > 0) BCK(b, cudaEventRecord(b->ev[si], st));
+            ++si;
+        }
+        for (int j = 1; j < si; ++j) BCK(b, cudaStreamWaitEvent(b->stream, b->ev[j], 0));
         b->t += chunk;
         n -= chunk;
     }
@@ -231,6 +264,7 @@ int read_status(ising_batch *b)
     BCK(b, cudaMemcpyAsync(&st, b->d_status, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
     BCK(b, cudaStreamSynchronize(b->stream));
     if (st == BATCH_STATUS_TIMEOUT) return bfail(b, ISING_ETIMEOUT, "a group barrier of the batch kernel timed out");
+    if (st) return bfail(b, ISING_ETIMEOUT, "fused sweep of a streamed class: a bounded wait for a copy gave up");
     return ISING_OK;
 }
 
@@ -248,6 +282,18 @@ int assign_modes(ising_batch *b)
         for (int r = 0; r < k.R; ++r)
             b->h_lats.push_back(BatchLattice{k.lat + (int64_t)r * 2 * g.nw, k.seed + (uint64_t)r, k.L, 0});
         if (lattice_bytes(k.L) <= 96 * 1024) max_local = std::max<int>(max_local, (int)lattice_bytes(k.L));
+    }
+    int nstreamed = 0;
+    for (const auto &k : b->cls) nstreamed += k.streamed;
+    while ((int)b->side.size() < nstreamed - 1) {
+        cudaStream_t st = nullptr;
+        BCK(b, cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        b->side.push_back(st);
+    }
+    while ((int)b->ev.size() < std::max(0, nstreamed)) {
+        cudaEvent_t e = nullptr;
+        BCK(b, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        b->ev.push_back(e);
     }
     cudaFree(b->d_lats);
     b->d_lats = nullptr;
@@ -294,7 +340,10 @@ int ising_batch_destroy(ising_batch *b)
         DevGuard dg(b->device);
         if (b->stream) cudaStreamSynchronize(b->stream);
         if (b->gexec) cudaGraphExecDestroy(b->gexec);
-        for (auto &k : b->cls) cudaFree(k.lat);
+        for (auto &k : b->cls) {
+            cudaFree(k.lat);
+            cudaFree(k.alt);
+        }
         cudaFree(b->d_lats);
         cudaFree(b->d_tasks);
         cudaFree(b->d_barriers);
@@ -302,6 +351,8 @@ int ising_batch_destroy(ising_batch *b)
         cudaFree(b->d_cta_ns);
         cudaFree(b->d_rec);
         cudaFree(b->d_der);
+        for (cudaStream_t st : b->side) cudaStreamDestroy(st);
+        for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
         if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     }
     delete b;
@@ -344,7 +395,8 @@ int ising_batch_create(ising_batch **out, int nclass, const int *L, const int *r
     }
     int64_t rec_off = 0, der_off = 0;
     for (int c = 0; c < nclass; ++c) {
-        BatchClass k{L[c], replicas[c], seeds[c], nullptr, rec_off, der_off, 0, SweepConfig{VARIANT_WORD, 0, 0, 0}};
+        BatchClass k{L[c], replicas[c], seeds[c], nullptr, rec_off, der_off, 0, SweepConfig{VARIANT_WORD, 0, 0, 0},
+                     nullptr};
         const int64_t bytes = lattice_bytes(L[c]) * replicas[c];
         if (cudaMalloc(&k.lat, (size_t)bytes) != cudaSuccess) {
             b->cls.push_back(k);
@@ -583,7 +635,87 @@ int ising_batch_tune(ising_batch *b, int probe_mcs, double *w_local_out)
         if ((s = build_plan(b)) != ISING_OK) return bfail(b, s, "plan");
         if ((s = upload_plan(b)) != ISING_OK) return s;
     }
+    // Streamed classes: candidates are the class's default kernel and the one the single-
+    // lattice autotuner picks for its size and replica count alone (timed on scratch
+    // contexts).  The streamed classes run side by side within a segment and compete for
+    // the SMs, so each class keeps the candidate with which the whole segment (every class)
+    // is fastest, one class after the other.
+    BCK(b, cudaStreamSynchronize(b->stream));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    BCK(b, cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return bfail(b, ISING_ECUDA, "event");
+    }
+    auto segment_ms = [&](float *ms) -> int {
+        int st = enqueue_segment(b, probe_mcs, nullptr);  // warm-up (first launches of a kernel)
+        if (st == ISING_OK && cudaEventRecord(e0, b->stream) != cudaSuccess) st = ISING_ECUDA;
+        if (st == ISING_OK) st = enqueue_segment(b, 2 * (int64_t)probe_mcs, nullptr);
+        if (st == ISING_OK && (cudaEventRecord(e1, b->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                               cudaEventElapsedTime(ms, e0, e1) != cudaSuccess))
+            st = ISING_ECUDA;
+        if (st == ISING_OK) st = read_status(b);
+        return st;
+    };
+    for (int c = 0; c < (int)b->cls.size() && s == ISING_OK; ++c) {
+        if (!b->cls[c].streamed) continue;
+        ising_opts base, alone, dflt;
+        ising_default_opts(&base);
+        base.tie = (ising_tie)b->rule;
+        base.device = b->device;
+        dflt = base;
+        if (ising_tune_sweep(b->cls[c].L, b->cls[c].R, probe_mcs, &base, &alone, nullptr) != ISING_OK) {
+            s = bfail(b, ISING_ECUDA, "tuning a streamed class");
+            break;
+        }
+        float ms_dflt = 0.f, ms_alone = 0.f;
+        if ((s = ising_batch_set_class_opts(b, c, &dflt)) != ISING_OK || (s = segment_ms(&ms_dflt)) != ISING_OK ||
+            (s = ising_batch_set_class_opts(b, c, &alone)) != ISING_OK || (s = segment_ms(&ms_alone)) != ISING_OK)
+            break;
+        if (ms_dflt <= ms_alone) s = ising_batch_set_class_opts(b, c, &dflt);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != ISING_OK) return s;
     if (w_local_out) *w_local_out = b->w_local;
+    return ISING_OK;
+}
+
+int ising_batch_set_class_opts(ising_batch *b, int cls, const ising_opts *o)
+{
+    int s = bcheck(b);
+    if (s) return s;
+    if (!o || cls < 0 || cls >= (int)b->cls.size()) return bfail(b, ISING_EINVAL, "bad class");
+    BatchClass &k = b->cls[cls];
+    if (!k.streamed) return bfail(b, ISING_EINVAL, "class is swept by the persistent kernel");
+    SweepConfig cfg{};
+    if (!resolve_sweep_config(k.L, k.R, o->variant, o->tile_y, o->tile_z, o->depth, &cfg))
+        return bfail(b, ISING_EINVAL, "sweep configuration not valid for this L");
+    DevGuard dg(b->device);
+    BCK(b, cudaStreamSynchronize(b->stream));
+    if (cfg.variant == VARIANT_ZFUSE && !k.alt &&
+        cudaMalloc(&k.alt, (size_t)(lattice_bytes(k.L) * k.R)) != cudaSuccess) {
+        k.alt = nullptr;
+        return bfail(b, ISING_ENOMEM, "second store of the fused sweep");
+    }
+    k.cfg = cfg;
+    if (b->gexec) {  // the cached schedule graph holds the old kernels
+        cudaGraphExecDestroy(b->gexec);
+        b->gexec = nullptr;
+        b->gkey.clear();
+    }
+    return ISING_OK;
+}
+
+int ising_batch_get_class_opts(const ising_batch *b, int cls, ising_opts *o)
+{
+    if (!b || !o || cls < 0 || cls >= (int)b->cls.size()) return ISING_EINVAL;
+    const BatchClass &k = b->cls[cls];
+    ising_default_opts(o);
+    o->variant = k.streamed ? k.cfg.variant : -1;
+    o->tile_y = k.cfg.tile_y;
+    o->tile_z = k.cfg.tile_z;
+    o->depth = k.cfg.depth;
     return ISING_OK;
 }
 

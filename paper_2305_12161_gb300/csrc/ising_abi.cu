@@ -99,6 +99,37 @@ size_t lattice_bytes_packed(int L, int R) { return (size_t)R * 2 * (size_t)make_
 
 }  // namespace
 
+namespace ising {
+
+// Kernel configuration of the packed sweep from the variant, tile and depth options
+// (variant 0: the default for L and R); false when it is not valid for L.
+bool resolve_sweep_config(int L, int R, int variant, int tile_y, int tile_z, int depth, SweepConfig *out)
+{
+    SweepConfig cfg{};
+    if (variant == 0) {
+        cfg = default_sweep_config(L, R);
+    } else {
+        cfg = SweepConfig{variant, tile_y, tile_z, variant == VARIANT_ZFUSE ? depth : (depth ? depth : 3)};
+        if ((cfg.variant == VARIANT_ZMARCH || cfg.variant == VARIANT_ZFAST || cfg.variant == VARIANT_ZDEEP ||
+             cfg.variant == VARIANT_ZFUSE) &&
+            (tile_y == 0 || tile_z == 0)) {
+            if (L >= 256 && L % 256 == 0) {
+                const int W4 = L / 256;
+                if (!cfg.tile_y) cfg.tile_y = std::max(1, 256 / W4);
+                if (!cfg.tile_z) cfg.tile_z = std::min(L, 16);
+            }
+        }
+        if ((cfg.variant == VARIANT_ZFAST || cfg.variant == VARIANT_ZDEEP || cfg.variant == VARIANT_ZFUSE) &&
+            L >= 256 && L % 256 == 0)
+            cfg.tile_y = 256 / (L / 256);
+        if (!sweep_config_valid(L, cfg)) return false;
+    }
+    *out = cfg;
+    return true;
+}
+
+}  // namespace ising
+
 extern "C" {
 
 void ising_default_opts(ising_opts *o)
@@ -210,24 +241,7 @@ int resolve_opts(int L, int R, const ising_opts &o, SweepConfig *cfg_out, DcbGeo
         (o.form != ISING_FORM_PACKED || !make_dcb_geom(L, o.block_x, o.block_y, o.block_z, &dcb)))
         return ISING_EINVAL;
     SweepConfig cfg{};
-    if (o.variant == 0) {
-        cfg = default_sweep_config(L, R);
-    } else {
-        cfg = SweepConfig{o.variant, o.tile_y, o.tile_z, o.variant == VARIANT_ZFUSE ? o.depth : (o.depth ? o.depth : 3)};
-        if ((cfg.variant == VARIANT_ZMARCH || cfg.variant == VARIANT_ZFAST || cfg.variant == VARIANT_ZDEEP ||
-             cfg.variant == VARIANT_ZFUSE) &&
-            (o.tile_y == 0 || o.tile_z == 0)) {
-            if (L >= 256 && L % 256 == 0) {
-                const int W4 = L / 256;
-                if (!cfg.tile_y) cfg.tile_y = std::max(1, 256 / W4);
-                if (!cfg.tile_z) cfg.tile_z = std::min(L, 16);
-            }
-        }
-        if ((cfg.variant == VARIANT_ZFAST || cfg.variant == VARIANT_ZDEEP || cfg.variant == VARIANT_ZFUSE) &&
-            L >= 256 && L % 256 == 0)
-            cfg.tile_y = 256 / (L / 256);
-        if (!sweep_config_valid(L, cfg)) return ISING_EINVAL;
-    }
+    if (!resolve_sweep_config(L, R, o.variant, o.tile_y, o.tile_z, o.depth, &cfg)) return ISING_EINVAL;
     if (cfg_out) *cfg_out = cfg;
     if (dcb_out) *dcb_out = dcb;
     return ISING_OK;
@@ -723,8 +737,10 @@ int ising_tune_sweep(int L, int replicas, int probe_mcs, const ising_opts *base,
                 if (sweep_config_valid(L, cd)) cands.push_back(cd);
             }
         }
-        for (int tz : {16, 32, 64, 128})
-            for (int mb : {1, 2, 3, 9, 10, 11, 19, 25, 26, 27}) {
+        // thin z-blocks (4, 8 planes) give small lattices enough tiles to fill the GPU
+        for (int tz : {4, 8, 16, 32, 64, 128})
+            for (int mb : {1, 2, 3, 9, 10, 11, 18, 19, 25, 26, 27}) {
+                if (tz < 16 && L > 512) continue;
                 const SweepConfig cf{VARIANT_ZFUSE, 256 / W4, tz, mb};
                 if (sweep_config_valid(L, cf)) cands.push_back(cf);
             }

@@ -118,18 +118,31 @@ __device__ __forceinline__ void fused_bulk(uint32_t dst, const void *src, uint32
                  : "memory");
 }
 
-// Arguments of one launch (one replica): kernel parameter space, so the Philox round keys
-// are read as constant-bank operands of the round's logic operations and take no registers.
-struct FusedArgs {
+// What differs between the replicas of a launch: kernel parameter space, so the Philox round
+// keys are read as constant-bank operands of the round's logic operations and take no
+// registers.
+struct FusedRep {
     PhiloxKeys keys;           // round keys of the replica's Philox key (seed + replica)
     PhiloxLead leadA, leadB;   // the draws' constant first rounds for sweep t, phases A and B
     const uint4 *Acur, *Bcur;  // store of sweep t: first-updated sublattice A and the other, B
     uint4 *Anxt, *Bnxt;        // store of sweep t + 1
+    uint32_t A;                // first sublattice (its tie-bit phase)
+};
+
+// Replicas one launch of the multi-replica form takes (grid.y); its parameters stay within
+// the classic 4 KB parameter space.
+constexpr int FUSED_MAXR = 16;
+
+// Arguments of one launch: MR = 1, one replica; MR = FUSED_MAXR, replica blockIdx.y of rep.
+template <int MR>
+struct FusedArgs {
+    FusedRep rep[MR];
     int L, nzb;                // z-blocks: block b holds planes b L / nzb .. (b + 1) L / nzb - 1
-    uint32_t t, A;             // sweep index, first sublattice (its tie-bit phase)
+    uint32_t t;                // sweep index
     int *err;                  // set to 4 when a bounded wait gave up
     uint64_t timeout_ns;
 };
+static_assert(sizeof(FusedArgs<FUSED_MAXR>) <= 4096, "multi-replica parameters exceed 4 KB");
 
 // Two tilings of the plane into row tiles.  First (BAL = false): a tile owns TY = 256 / W4
 // rows y0 .. y0 + TY - 1, one per thread row, and lanes 0 .. 2 W4 - 1 of warp 0 also update A
@@ -164,8 +177,8 @@ static constexpr size_t fused_smem_bytes()
 // step comes from shared memory (nothing is carried across steps in registers), and the
 // steps are unrolled in pairs so that the x direction P of the pair's two planes is a
 // compile-time constant.  Offsets into a sublattice are 32-bit uint4 indices (L^3 / 256 < 2^31).
-template <int RULE, int W4, int NS, int MINB, bool BAL>
-__global__ void __launch_bounds__(256, MINB) k_mcs_fused(const __grid_constant__ FusedArgs fa)
+template <int RULE, int W4, int NS, int MINB, bool BAL, int MR>
+__global__ void __launch_bounds__(256, MINB) k_mcs_fused(const __grid_constant__ FusedArgs<MR> fa)
 {
     // first step whose wait gave up in some thread (0x7fffffff: none); every thread reads it
     // after the step's barrier and leaves when it is at or before its own step, so a failure
@@ -182,6 +195,7 @@ __global__ void __launch_bounds__(256, MINB) k_mcs_fused(const __grid_constant__
     uint4 *ring = fsm;                   // [NS][SLOT], group g in slot g % NS
     uint4 *anew = fsm + NS * SLOT;       // [3][NEW], plane zA in slot k % 3
     uint64_t *full = reinterpret_cast<uint64_t *>(anew + 3 * NEW);  // [NS]
+    const FusedRep &rp = fa.rep[MR == 1 ? 0 : blockIdx.y];
     const int L = fa.L;
     const int tid = threadIdx.x;
     const int nty = (L + TYO - 1) / TYO;
@@ -217,8 +231,8 @@ __global__ void __launch_bounds__(256, MINB) k_mcs_fused(const __grid_constant__
         const uint32_t bytes = (uint32_t)(16 * (NB + (g >= 2 ? RA * W4 : 0)));
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
         const uint32_t dst = ring0 + (uint32_t)(16 * sl * SLOT);
-        copy_rows(dst, fa.Bcur + wrapL(z0 - 2 + g) * plane4, y0 - 2, RB, mbar);
-        if (g >= 2) copy_rows(dst + 16u * NB, fa.Acur + wrapL(z0 - 3 + g) * plane4, y0 - 1, RA, mbar);
+        copy_rows(dst, rp.Bcur + wrapL(z0 - 2 + g) * plane4, y0 - 2, RB, mbar);
+        if (g >= 2) copy_rows(dst + 16u * NB, rp.Acur + wrapL(z0 - 3 + g) * plane4, y0 - 1, RA, mbar);
     };
     if (tid == 0) {
         s_fail = 0x7fffffff;
@@ -248,7 +262,7 @@ __global__ void __launch_bounds__(256, MINB) k_mcs_fused(const __grid_constant__
     const int hB = (hr ? NR + 2 : 1) * W4 + cx;  // halo row in a B slot
     const int hN = (hr ? NR + 1 : 0) * W4 + cx;  // halo row in an A slot
     const int32_t dh = wrapL(hr ? y0 + NR : y0 - 1) * W4 + cx - own;
-    const uint32_t A = fa.A, B = 1u - fa.A;
+    const uint32_t A = rp.A, B = 1u - rp.A;
 
     // groups 0 and 1 before the first step (step k waits for group k + 2); thread 0 tracks
     // the last group it saw land and the last it issued, for the drain after a failed wait
@@ -283,9 +297,9 @@ __global__ void __launch_bounds__(256, MINB) k_mcs_fused(const __grid_constant__
             const uint32_t e = __shfl_sync(FULL, P ? bc.x : bc.w, P ? srcr : srcl, W4);
             const uint4 X = xshift(bc, e, e, P);
             a0 = fused_spins4<RULE>(S2[NB + rN], bc, X, S1[rB - W4], S1[rB + W4], bm, S2[rB],
-                                                (uint32_t)oA, fa.leadA, fa.keys);
+                                                (uint32_t)oA, rp.leadA, rp.keys);
             An[rN] = a0;
-            if (bown && k >= 1 && k <= TZ) fa.Anxt[oA] = a0;
+            if (bown && k >= 1 && k <= TZ) rp.Anxt[oA] = a0;
         }
         // first tiling, A on the halo rows: row y0 - 1 is odd (the other direction than warp
         // 0's even rows), row y0 + NR even (the same)
@@ -295,7 +309,7 @@ __global__ void __launch_bounds__(256, MINB) k_mcs_fused(const __grid_constant__
             const uint32_t e = __shfl_sync(HMASK, ph ? hbc.x : hbc.w, ph ? srcr : srcl, W4);
             const uint4 X = xshift(hbc, e, e, ph);
             An[hN] = fused_spins4<RULE>(S2[NB + hN], hbc, X, S1[hB - W4], S1[hB + W4], S0[hB], S2[hB],
-                                                    (uint32_t)(oA + dh), fa.leadA, fa.keys);
+                                                    (uint32_t)(oA + dh), rp.leadA, rp.keys);
         }
         // B on plane zB = zA - 1, own column: new A of planes zB - 1, zB, zB + 1 are in the
         // new-A slots of steps k - 2 and k - 1, and a0
@@ -306,9 +320,9 @@ __global__ void __launch_bounds__(256, MINB) k_mcs_fused(const __grid_constant__
             const uint32_t e = __shfl_sync(FULL, P ? a1.x : a1.w, P ? srcr : srcl, W4);
             const uint4 X = xshift(a1, e, e, P);
             const int32_t oB = oA >= plane4 ? oA - plane4 : oA - plane4 + vol4;
-            const uint4 nb = fused_spins4<RULE>(bm, a1, X, A1[rNm], A1[rNp], A2[rN], a0, (uint32_t)oB, fa.leadB,
-                                                fa.keys);
-            if (bown) fa.Bnxt[oB] = nb;
+            const uint4 nb = fused_spins4<RULE>(bm, a1, X, A1[rNm], A1[rNp], A2[rN], a0, (uint32_t)oB, rp.leadB,
+                                                rp.keys);
+            if (bown) rp.Bnxt[oB] = nb;
         }
         oA += plane4;
         if (oA >= vol4) oA -= vol4;
@@ -384,63 +398,94 @@ static PhiloxKeys host_round_keys(uint64_t S)
     return k;
 }
 
-// One launch per replica: its round keys and first sublattice travel as kernel parameters.
-template <int RULE, int W4, int NS, bool BAL>
+// Kernel attributes of one instantiation, set once per process (the first call of a form).
+template <class K>
+static cudaError_t fused_attrs(K kern, size_t smem)
+{
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    return e;
+}
+
+static FusedRep fused_rep(const uint32_t *cur, uint32_t *nxt, int64_t nw, int r, uint64_t seed, int mixed,
+                          uint32_t t)
+{
+    const uint64_t S = seed + (uint64_t)r;
+    FusedRep a;
+    a.keys = host_round_keys(S);
+    a.A = mixed ? (uint32_t)mixed_first(S, t) : 0u;
+    a.leadA = philox_lead(t, a.A, a.keys);
+    a.leadB = philox_lead(t, 1u - a.A, a.keys);
+    a.Acur = reinterpret_cast<const uint4 *>(cur + (2 * (int64_t)r + a.A) * nw);
+    a.Bcur = reinterpret_cast<const uint4 *>(cur + (2 * (int64_t)r + 1 - a.A) * nw);
+    a.Anxt = reinterpret_cast<uint4 *>(nxt + (2 * (int64_t)r + a.A) * nw);
+    a.Bnxt = reinterpret_cast<uint4 *>(nxt + (2 * (int64_t)r + 1 - a.A) * nw);
+    return a;
+}
+
+// One sweep of R replicas.  MULTI: up to FUSED_MAXR replicas per launch along grid.y, each
+// with its own round keys, first sublattice and stores in the parameter array (for many
+// small lattices, whose single-replica grids would leave most SMs idle); otherwise one launch
+// per replica with its arguments as the kernel's only parameters.
+template <int RULE, int W4, int NS, bool BAL, bool MULTI>
 static cudaError_t fused_rule(const uint32_t *cur, uint32_t *nxt, int L, int R, uint64_t seed, int mixed, uint32_t t,
                               int TZ, bool fit, int *err, uint64_t timeout_ns, cudaStream_t s)
 {
+    constexpr int MR = MULTI ? FUSED_MAXR : 1;
     constexpr size_t smem = fused_smem_bytes<W4, NS, BAL>();
     // CTAs per SM that the shared memory allows (228 KB per SM, 1 KB reserved per CTA); the
     // registers are capped to match
     constexpr int MINB = (int)(233472 / (smem + 1024)) >= 4 ? 4 : 3;
-    auto kern = k_mcs_fused<RULE, W4, NS, MINB, BAL>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    auto kern = k_mcs_fused<RULE, W4, NS, MINB, BAL, MR>;
+    cudaError_t e = fused_attrs(kern, smem);
     if (e != cudaSuccess) return e;
     const Geom g = make_geom(L);
     constexpr int TYO = FusedTile<W4, BAL>::TYO;
     const int nty = (L + TYO - 1) / TYO;
+    const int per_launch = MULTI ? std::min(R, FUSED_MAXR) : 1;
     int nzb = L / TZ;
     if (fit) {
         int per_sm = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
         if (e != cudaSuccess) return e;
-        nzb = fitted_zblocks(L, TZ, nty, std::max(1, per_sm) * device_sms());
+        nzb = fitted_zblocks(L, TZ, nty * per_launch, std::max(1, per_sm) * device_sms());
     }
-    const dim3 grid((unsigned)(nty * nzb));
-    for (int r = 0; r < R; ++r) {
-        const uint64_t S = seed + (uint64_t)r;
-        FusedArgs a;
-        a.keys = host_round_keys(S);
-        a.A = mixed ? (uint32_t)mixed_first(S, t) : 0u;
-        a.leadA = philox_lead(t, a.A, a.keys);
-        a.leadB = philox_lead(t, 1u - a.A, a.keys);
-        a.Acur = reinterpret_cast<const uint4 *>(cur + (2 * (int64_t)r + a.A) * g.nw);
-        a.Bcur = reinterpret_cast<const uint4 *>(cur + (2 * (int64_t)r + 1 - a.A) * g.nw);
-        a.Anxt = reinterpret_cast<uint4 *>(nxt + (2 * (int64_t)r + a.A) * g.nw);
-        a.Bnxt = reinterpret_cast<uint4 *>(nxt + (2 * (int64_t)r + 1 - a.A) * g.nw);
+    for (int r0 = 0; r0 < R; r0 += per_launch) {
+        const int nr = std::min(per_launch, R - r0);
+        FusedArgs<MR> a;
+        for (int i = 0; i < nr; ++i) a.rep[i] = fused_rep(cur, nxt, g.nw, r0 + i, seed, mixed, t);
         a.L = L;
         a.nzb = nzb;
         a.t = t;
         a.err = err;
         a.timeout_ns = timeout_ns;
-        kern<<<grid, 256, smem, s>>>(a);
+        kern<<<dim3((unsigned)(nty * nzb), (unsigned)nr), 256, smem, s>>>(a);
     }
     return cudaGetLastError();
 }
 
-template <int RULE, int NS, bool BAL>
+template <int RULE, int NS, bool BAL, bool MULTI>
 static cudaError_t fused_one(const uint32_t *cur, uint32_t *nxt, int L, int R, uint64_t seed, int mixed, uint32_t t,
                              int TZ, bool fit, int *err, uint64_t timeout_ns, cudaStream_t s)
 {
     switch (L / 256) {
-    case 1: return fused_rule<RULE, 1, NS, BAL>(cur, nxt, L, R, seed, mixed, t, TZ, fit, err, timeout_ns, s);
-    case 2: return fused_rule<RULE, 2, NS, BAL>(cur, nxt, L, R, seed, mixed, t, TZ, fit, err, timeout_ns, s);
-    case 4: return fused_rule<RULE, 4, NS, BAL>(cur, nxt, L, R, seed, mixed, t, TZ, fit, err, timeout_ns, s);
-    case 8: return fused_rule<RULE, 8, NS, BAL>(cur, nxt, L, R, seed, mixed, t, TZ, fit, err, timeout_ns, s);
+    case 1: return fused_rule<RULE, 1, NS, BAL, MULTI>(cur, nxt, L, R, seed, mixed, t, TZ, fit, err, timeout_ns, s);
+    case 2: return fused_rule<RULE, 2, NS, BAL, MULTI>(cur, nxt, L, R, seed, mixed, t, TZ, fit, err, timeout_ns, s);
+    case 4: return fused_rule<RULE, 4, NS, BAL, MULTI>(cur, nxt, L, R, seed, mixed, t, TZ, fit, err, timeout_ns, s);
+    case 8: return fused_rule<RULE, 8, NS, BAL, MULTI>(cur, nxt, L, R, seed, mixed, t, TZ, fit, err, timeout_ns, s);
     default: return cudaErrorInvalidValue;
     }
+}
+
+// Five-slot forms: several replicas per launch when there are several (the multi-replica
+// kernel is built for these forms only).
+template <int RULE, bool BAL>
+static cudaError_t fused_five(const uint32_t *cur, uint32_t *nxt, int L, int R, uint64_t seed, int mixed, uint32_t t,
+                              int TZ, bool fit, int *err, uint64_t timeout_ns, cudaStream_t s)
+{
+    if (R > 1) return fused_one<RULE, 5, BAL, true>(cur, nxt, L, R, seed, mixed, t, TZ, fit, err, timeout_ns, s);
+    return fused_one<RULE, 5, BAL, false>(cur, nxt, L, R, seed, mixed, t, TZ, fit, err, timeout_ns, s);
 }
 
 // depth = copy groups in flight while a step computes: 1..3 (four to six slots; 0 = 2); +8:
@@ -451,14 +496,23 @@ static cudaError_t fused_depth(const uint32_t *cur, uint32_t *nxt, int L, int R,
 {
     const bool fit = depth & 16;
     switch (depth & ~16) {
-    case 1: return fused_one<RULE, 4, false>(cur, nxt, L, R, seed, mixed, t, TZ, fit, err, timeout_ns, s);
-    case 3: return fused_one<RULE, 6, false>(cur, nxt, L, R, seed, mixed, t, TZ, fit, err, timeout_ns, s);
-    case 9: return fused_one<RULE, 4, true>(cur, nxt, L, R, seed, mixed, t, TZ, fit, err, timeout_ns, s);
+    case 1: return fused_one<RULE, 4, false, false>(cur, nxt, L, R, seed, mixed, t, TZ, fit, err, timeout_ns, s);
+    case 3: return fused_one<RULE, 6, false, false>(cur, nxt, L, R, seed, mixed, t, TZ, fit, err, timeout_ns, s);
+    case 9: return fused_one<RULE, 4, true, false>(cur, nxt, L, R, seed, mixed, t, TZ, fit, err, timeout_ns, s);
     case 8:
-    case 10: return fused_one<RULE, 5, true>(cur, nxt, L, R, seed, mixed, t, TZ, fit, err, timeout_ns, s);
-    case 11: return fused_one<RULE, 6, true>(cur, nxt, L, R, seed, mixed, t, TZ, fit, err, timeout_ns, s);
-    default: return fused_one<RULE, 5, false>(cur, nxt, L, R, seed, mixed, t, TZ, fit, err, timeout_ns, s);
+    case 10: return fused_five<RULE, true>(cur, nxt, L, R, seed, mixed, t, TZ, fit, err, timeout_ns, s);
+    case 11: return fused_one<RULE, 6, true, false>(cur, nxt, L, R, seed, mixed, t, TZ, fit, err, timeout_ns, s);
+    default: return fused_five<RULE, false>(cur, nxt, L, R, seed, mixed, t, TZ, fit, err, timeout_ns, s);
     }
+}
+
+// Launches of one sweep of R replicas: the five-slot forms take up to FUSED_MAXR replicas per
+// launch, the others one.
+static int64_t fused_launches_per_sweep(int R, int depth)
+{
+    const int d = depth & ~16;
+    const bool five = !(d == 1 || d == 3 || d == 9 || d == 11);
+    return five && R > 1 ? (R + FUSED_MAXR - 1) / FUSED_MAXR : R;
 }
 
 cudaError_t launch_sweeps_fused(uint32_t **cur, uint32_t **nxt, int L, int R, uint64_t seed, int rule, int64_t t0,
@@ -482,7 +536,7 @@ cudaError_t launch_sweeps_fused(uint32_t **cur, uint32_t **nxt, int L, int R, ui
         uint32_t *tmp = *cur;  // the new sweep becomes the current store
         *cur = *nxt;
         *nxt = tmp;
-        if (launches) *launches += R;
+        if (launches) *launches += fused_launches_per_sweep(R, depth);
     }
     return cudaSuccess;
 }

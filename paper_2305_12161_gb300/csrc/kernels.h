@@ -30,6 +30,7 @@ struct SweepConfig {
 
 bool sweep_config_valid(int L, const SweepConfig &c);
 SweepConfig default_sweep_config(int L, int R);
+bool resolve_sweep_config(int L, int R, int variant, int tile_y, int tile_z, int depth, SweepConfig *out);
 
 // Fused sweeps (VARIANT_ZFUSE): each sweep reads *cur and writes *nxt, then swaps the two
 // pointers, so after n sweeps *cur holds the state.  Both stores hold 2*R*nw words.

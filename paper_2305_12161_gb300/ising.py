@@ -112,6 +112,8 @@ def lib() -> ctypes.CDLL:
                 "ising_batch_tune": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
                 "ising_batch_set_weights": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_double]),
                 "ising_batch_set_streamed": (ctypes.c_int, [vp, ctypes.c_int]),
+                "ising_batch_set_class_opts": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ising_opts)]),
+                "ising_batch_get_class_opts": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ising_opts)]),
                 "ising_batch_streamed_classes": (ctypes.c_int, [vp]),
                 "ising_batch_inject_missing_cta": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_double]),
                 "ising_batch_last_error": (ctypes.c_char_p, [vp]),
@@ -471,8 +473,21 @@ class Batch:
         self._check(lib().ising_batch_set_weights(self._h, w_local, w_group), "ising_batch_set_weights")
 
     def set_streamed(self, min_L: int) -> None:
-        """Classes with L >= min_L (L % 256 == 0) use the z-marching kernel; <= 0: none."""
+        """Classes with L >= min_L (L % 256 == 0) use a single-lattice kernel; <= 0: none."""
         self._check(lib().ising_batch_set_streamed(self._h, min_L), "ising_batch_set_streamed")
+
+    def set_class_config(self, cls: int, variant: int = 0, tile_y: int = 0, tile_z: int = 0, depth: int = 0) -> None:
+        """Sweep kernel of streamed class ``cls`` (ising_batch_set_class_opts)."""
+        o = ising_opts()
+        lib().ising_default_opts(ctypes.byref(o))
+        o.variant, o.tile_y, o.tile_z, o.depth = variant, tile_y, tile_z, depth
+        self._check(lib().ising_batch_set_class_opts(self._h, cls, ctypes.byref(o)), "ising_batch_set_class_opts")
+
+    def class_config(self, cls: int) -> dict:
+        """Sweep kernel of class ``cls``: variant -1 for the persistent kernel."""
+        o = ising_opts()
+        self._check(lib().ising_batch_get_class_opts(self._h, cls, ctypes.byref(o)), "ising_batch_get_class_opts")
+        return dict(variant=o.variant, tile_y=o.tile_y, tile_z=o.tile_z, depth=o.depth)
 
     def streamed_classes(self) -> int:
         return int(lib().ising_batch_streamed_classes(self._h))

@@ -115,10 +115,14 @@ def test_tuned_plan_changes_speed_not_results(ising):
         w = b.tune(probe_mcs=2)
         assert w > 0
         t_after = b.t
+        kern = b.class_config(2)
         b.reinit()
         b.sweep(6)
         got = [b.get_packed(ci, r) for ci, (L, R, s) in enumerate(classes) for r in range(R)]
-        assert t_after == 6
+        # three work-list rounds of 2 MCS, then for the one streamed class two candidates,
+        # each timed as a warm-up segment of 2 MCS and a timed one of 4
+        assert t_after == 6 + 2 * (2 + 4)
+        assert kern["variant"] > 0 and b.class_config(0)["variant"] == -1
         for x, y in zip(got, ref):
             assert np.array_equal(x, y)
         for wl in (0.25, 4.0):
