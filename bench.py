@@ -196,6 +196,7 @@ def run_batched(torch, ising, inputs, K: int = 20, window: int = 20) -> dict:
         out["autotuner_w_local"] = w
         out["plan"] = bt.plan()
         kernels = [bt.class_config(ci) for ci in range(len(BATCH_CLASSES))]
+        out["streamed_beside_persistent"] = bt.overlap
         out["class_kernels"] = {f"{L}^3": ("persistent" if k["variant"] < 0 else
                                            f"variant {k['variant']}, tile_z {k['tile_z']}, depth {k['depth']}")
                                 for (L, _, _), k in zip(BATCH_CLASSES, kernels)}

@@ -338,7 +338,9 @@ int ising_batch_plan(const ising_batch *b, int *ntasks, int *nlocal, int *ngroup
  * class, one after the other, keeps whichever of its default kernel and the kernel that
  * ising_tune_sweep picks for its L and replica count alone gives the faster whole segment
  * (the streamed classes of a segment run side by side on their own streams, forked from
- * and joined back into the batch's stream, so they compete for the SMs). */
+ * and joined back into the batch's stream, so they compete for the SMs); last, it keeps
+ * the faster of the streamed classes beside or after the persistent launch
+ * (ising_batch_set_overlap). */
 int ising_batch_tune(ising_batch *b, int probe_mcs, double *w_local_out);
 /* Sweep kernel of streamed class `cls` (Methods, "Checkerboard update"; every choice gives
  * the same trajectory): opts->variant, tile_y, tile_z and depth as for ising_create_ex,
@@ -354,6 +356,13 @@ int ising_batch_set_class_opts(ising_batch *b, int cls, const ising_opts *opts);
 /* The sweep kernel of class `cls` into opts (variant -1: the class is swept by the
  * persistent kernel); ISING_EINVAL for a bad class or NULL pointer. */
 int ising_batch_get_class_opts(const ising_batch *b, int cls, ising_opts *opts);
+/* on = 1: within a segment the streamed classes run beside the persistent launch (every one
+ * on a side stream forked before it); on = 0 (the default): after it.  The lattices of the
+ * two parts are disjoint, so the results are the same either way; ising_batch_tune keeps the
+ * faster.  ISING_EINVAL unless on is 0 or 1.  Drops the cached schedule graph. */
+int ising_batch_set_overlap(ising_batch *b, int on);
+/* The current setting of ising_batch_set_overlap (-1 for a NULL batch). */
+int ising_batch_overlap(const ising_batch *b);
 int ising_batch_set_weights(ising_batch *b, double w_local, double w_group);
 /* Classes with L >= min_L and L % 256 == 0 are swept by a single-lattice kernel, the
  * others by the persistent kernel; min_L <= 0 puts every class in the persistent kernel.

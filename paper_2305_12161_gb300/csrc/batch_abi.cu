@@ -27,6 +27,7 @@ struct BatchClass {
     int streamed;        // swept by a single-lattice sweep kernel instead of the persistent one
     SweepConfig cfg;     // that kernel's configuration (streamed classes)
     uint32_t *alt;       // second store of the fused whole-sweep kernel (allocated when chosen)
+    uint32_t *xt;        // tensor-core correlation scratch (L >= 512), else null: bit counts
 };
 
 bool packed_L_ok(int L) { return (L >= 64 && L % 64 == 0) || L == 4 || L == 8 || L == 16 || L == 32; }
@@ -37,10 +38,13 @@ struct ising_batch {
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
-    // streamed classes after the first run on side streams forked from and joined back into
-    // `stream` within each segment (ev[0]: fork, ev[1 + i]: join of side[i])
+    // streamed classes run on side streams forked from and joined back into `stream` within
+    // each segment (ev[0]: fork, ev[1 + i]: join of side[i]); with `overlap` every streamed
+    // class has a side stream and runs beside the persistent launch, otherwise the first
+    // one runs on `stream` after it.  Measurements fork one class per stream the same way.
     std::vector<cudaStream_t> side;
     std::vector<cudaEvent_t> ev;
+    int overlap = 0;
     int rule = 0;
     std::vector<BatchClass> cls;
     int64_t nlat = 0, rec_words = 0;
@@ -201,23 +205,31 @@ int enqueue_segment(ising_batch *b, int64_t n, unsigned long long *cta_ns)
 {
     while (n > 0) {
         const int chunk = (int)std::min<int64_t>(n, 1 << 30);
-        if (!b->h_tasks.empty()) {
+        int nstreamed = 0, si = 0;
+        for (const auto &k : b->cls) nstreamed += k.streamed;
+        const bool persistent = !b->h_tasks.empty();
+        // side streams: every streamed class when they overlap the persistent launch, else all
+        // but the first, which follows the persistent launch on the batch's stream
+        const int first_side = (b->overlap && persistent) ? 0 : 1;
+        // fork before the persistent launch when the streamed classes overlap it, after it
+        // otherwise
+        if (first_side == 0 && nstreamed > 0) BCK(b, cudaEventRecord(b->ev[0], b->stream));
+        if (persistent) {
             BCK(b, cudaMemsetAsync(b->d_barriers, 0, sizeof(unsigned) * (size_t)std::max(1, b->ngroups), b->stream));
             BCK(b, launch_batch(b->d_tasks, (int)b->h_tasks.size(), b->d_lats, b->rule, (uint32_t)b->t, chunk,
                                 b->d_barriers, b->d_status, b->timeout_ns, b->missing_cta, cta_ns, b->smem,
                                 b->stream));
             b->launches += 1;
         }
+        if (first_side == 1 && nstreamed > 1) BCK(b, cudaEventRecord(b->ev[0], b->stream));
         // the streamed classes, each on its own stream: their short launches (a few
         // microseconds of work each) overlap instead of waiting for one another
-        int nstreamed = 0, si = 0;
-        for (const auto &k : b->cls) nstreamed += k.streamed;
-        if (nstreamed > 1) BCK(b, cudaEventRecord(b->ev[0], b->stream));
         for (const auto &k : b->cls) {
             if (!k.streamed) continue;
+            const int sj = si + (1 - first_side);  // side stream index + 1 (0: the batch's stream)
             cudaStream_t st = b->stream;
-            if (si > 0) {
-                st = b->side[si - 1];
+            if (sj > 0) {
+                st = b->side[sj - 1];
                 BCK(b, cudaStreamWaitEvent(st, b->ev[0], 0));
             }
             if (k.cfg.variant == VARIANT_ZFUSE) {
@@ -236,10 +248,10 @@ int enqueue_segment(ising_batch *b, int64_t n, unsigned long long *cta_ns)
                 BCK(b, launch_sweeps_packed(k.lat, k.L, k.R, k.seed, b->rule, b->t, chunk, 0, k.cfg, st,
                                             &b->launches));
             }
-            if (si > 0) BCK(b, cudaEventRecord(b->ev[si], st));
+            if (sj > 0) BCK(b, cudaEventRecord(b->ev[sj], st));
             ++si;
         }
-        for (int j = 1; j < si; ++j) BCK(b, cudaStreamWaitEvent(b->stream, b->ev[j], 0));
+        for (int j = 1; j <= si - first_side; ++j) BCK(b, cudaStreamWaitEvent(b->stream, b->ev[j], 0));
         b->t += chunk;
         n -= chunk;
     }
@@ -248,13 +260,24 @@ int enqueue_segment(ising_batch *b, int64_t n, unsigned long long *cta_ns)
 
 int enqueue_measure(ising_batch *b, int64_t *rec, double *der, double c, unsigned flags)
 {
+    // one class per stream (class 0 on the batch's stream, class i on side stream i - 1): the
+    // classes write disjoint parts of rec and der and share no scratch
     const bool corr = !(flags & ISING_MEAS_NO_CORR);
-    for (const auto &k : b->cls) {
-        BCK(b, launch_measure(k.lat, k.L, k.R, b->t, corr, rec + k.rec_off, b->stream, &b->launches));
+    const int nc = (int)b->cls.size();
+    if (nc > 1) BCK(b, cudaEventRecord(b->ev[0], b->stream));
+    for (int i = 0; i < nc; ++i) {
+        const auto &k = b->cls[i];
+        cudaStream_t st = i == 0 ? b->stream : b->side[i - 1];
+        if (i > 0) BCK(b, cudaStreamWaitEvent(st, b->ev[0], 0));
+        const int method = !corr ? CORR_NONE : (k.xt ? CORR_TENSOR : CORR_POPCOUNT);
+        BCK(b, launch_measure(k.lat, k.L, k.R, b->t, method, rec + k.rec_off, st, &b->launches, k.xt, b->d_status,
+                              (double)b->timeout_ns * 1e-9));
         if (der)
             BCK(b, launch_derived(rec + k.rec_off, k.L, k.R, c, flags & ISING_MEAS_CONNECTED, der + 4 * k.der_off,
-                                  b->stream, &b->launches));
+                                  st, &b->launches));
+        if (i > 0) BCK(b, cudaEventRecord(b->ev[i], st));
     }
+    for (int i = 1; i < nc; ++i) BCK(b, cudaStreamWaitEvent(b->stream, b->ev[i], 0));
     return ISING_OK;
 }
 
@@ -263,8 +286,13 @@ int read_status(ising_batch *b)
     int st = 0;
     BCK(b, cudaMemcpyAsync(&st, b->d_status, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
     BCK(b, cudaStreamSynchronize(b->stream));
-    if (st == BATCH_STATUS_TIMEOUT) return bfail(b, ISING_ETIMEOUT, "a group barrier of the batch kernel timed out");
-    if (st) return bfail(b, ISING_ETIMEOUT, "fused sweep of a streamed class: a bounded wait for a copy gave up");
+    // status codes: 1 a group barrier of the batch kernel (or the first wait of a tensor-core
+    // correlation CTA) ran out, 2 and 3 later waits of the tensor-core correlation, 4 a copy
+    // wait of the fused sweep
+    if (st == BATCH_STATUS_TIMEOUT)
+        return bfail(b, ISING_ETIMEOUT, "a group barrier of the batch kernel or a correlation wait timed out");
+    if (st == 4) return bfail(b, ISING_ETIMEOUT, "fused sweep of a streamed class: a bounded wait for a copy gave up");
+    if (st) return bfail(b, ISING_ETIMEOUT, "tensor-core correlation: a bounded device-side wait gave up");
     return ISING_OK;
 }
 
@@ -285,12 +313,15 @@ int assign_modes(ising_batch *b)
     }
     int nstreamed = 0;
     for (const auto &k : b->cls) nstreamed += k.streamed;
-    while ((int)b->side.size() < nstreamed - 1) {
+    // side streams: one per streamed class (segments) and one per class after the first
+    // (measurements)
+    const int nside = std::max(nstreamed, (int)b->cls.size() - 1);
+    while ((int)b->side.size() < nside) {
         cudaStream_t st = nullptr;
         BCK(b, cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
         b->side.push_back(st);
     }
-    while ((int)b->ev.size() < std::max(0, nstreamed)) {
+    while ((int)b->ev.size() < nside + 1) {
         cudaEvent_t e = nullptr;
         BCK(b, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         b->ev.push_back(e);
@@ -343,6 +374,7 @@ int ising_batch_destroy(ising_batch *b)
         for (auto &k : b->cls) {
             cudaFree(k.lat);
             cudaFree(k.alt);
+            cudaFree(k.xt);
         }
         cudaFree(b->d_lats);
         cudaFree(b->d_tasks);
@@ -396,9 +428,20 @@ int ising_batch_create(ising_batch **out, int nclass, const int *L, const int *r
     int64_t rec_off = 0, der_off = 0;
     for (int c = 0; c < nclass; ++c) {
         BatchClass k{L[c], replicas[c], seeds[c], nullptr, rec_off, der_off, 0, SweepConfig{VARIANT_WORD, 0, 0, 0},
-                     nullptr};
+                     nullptr, nullptr};
         const int64_t bytes = lattice_bytes(L[c]) * replicas[c];
         if (cudaMalloc(&k.lat, (size_t)bytes) != cudaSuccess) {
+            b->cls.push_back(k);
+            return bail(ISING_ENOMEM);
+        }
+        // L >= 512: the correlation sums on the tensor cores, as a single context chooses them
+        // (far faster than bit counts there); the scratch is allocated here, never while a
+        // schedule is being captured
+        if (L[c] >= 512 && corr_mma_supported(L[c]) &&
+            cudaMalloc(&k.xt, corr_mma_scratch_bytes(L[c], replicas[c])) != cudaSuccess) {
+            k.xt = nullptr;
+            cudaFree(k.lat);
+            k.lat = nullptr;
             b->cls.push_back(k);
             return bail(ISING_ENOMEM);
         }
@@ -674,6 +717,14 @@ int ising_batch_tune(ising_batch *b, int probe_mcs, double *w_local_out)
             break;
         if (ms_dflt <= ms_alone) s = ising_batch_set_class_opts(b, c, &dflt);
     }
+    // the streamed classes beside the persistent launch, or after it
+    if (s == ISING_OK && !b->h_tasks.empty() && ising_batch_streamed_classes(b) > 0) {
+        float ms_after = 0.f, ms_beside = 0.f;
+        if ((s = ising_batch_set_overlap(b, 0)) == ISING_OK && (s = segment_ms(&ms_after)) == ISING_OK &&
+            (s = ising_batch_set_overlap(b, 1)) == ISING_OK && (s = segment_ms(&ms_beside)) == ISING_OK &&
+            ms_after <= ms_beside)
+            s = ising_batch_set_overlap(b, 0);
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (s != ISING_OK) return s;
@@ -706,6 +757,24 @@ int ising_batch_set_class_opts(ising_batch *b, int cls, const ising_opts *o)
     }
     return ISING_OK;
 }
+
+int ising_batch_set_overlap(ising_batch *b, int on)
+{
+    int s = bcheck(b);
+    if (s) return s;
+    if (on != 0 && on != 1) return bfail(b, ISING_EINVAL, "overlap must be 0 or 1");
+    DevGuard dg(b->device);
+    BCK(b, cudaStreamSynchronize(b->stream));
+    b->overlap = on;
+    if (b->gexec) {  // the cached schedule graph holds the old stream order
+        cudaGraphExecDestroy(b->gexec);
+        b->gexec = nullptr;
+        b->gkey.clear();
+    }
+    return ISING_OK;
+}
+
+int ising_batch_overlap(const ising_batch *b) { return b ? b->overlap : -1; }
 
 int ising_batch_get_class_opts(const ising_batch *b, int cls, ising_opts *o)
 {

@@ -239,6 +239,27 @@ __device__ __forceinline__ uint32_t resolve(uint32_t s, uint32_t ge4, uint32_t e
     return ge4 | (eq3 & tie);
 }
 
+// Programmatic dependent launch (a kernel launched with the programmatic stream
+// serialisation attribute may be scheduled while the previous kernel of its stream drains):
+// wait until the previous grid has completed and its memory operations are visible, then let
+// the next grid of the stream start its own launch.  Executed first, before any access to
+// global memory, so the kernel sees exactly what an ordinary stream order would give it;
+// without the attribute both are no-ops.
+__device__ __forceinline__ void pdl_enter()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Launch attribute of the kernels that begin with pdl_enter().
+inline cudaLaunchAttribute pdl_attribute()
+{
+    cudaLaunchAttribute a;
+    a.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    a.val.programmaticStreamSerializationAllowed = 1;
+    return a;
+}
+
 __device__ __forceinline__ uint32_t maj3(uint32_t a, uint32_t b, uint32_t c) { return (a & b) | (c & (a ^ b)); }
 
 // New spins of the 128 sites of one uint4 (T -> 0 Glauber, Eq. 6).  With u the number of up

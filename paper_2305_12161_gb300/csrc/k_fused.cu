@@ -195,6 +195,7 @@ __global__ void __launch_bounds__(256, MINB) k_mcs_fused(const __grid_constant__
     uint4 *ring = fsm;                   // [NS][SLOT], group g in slot g % NS
     uint4 *anew = fsm + NS * SLOT;       // [3][NEW], plane zA in slot k % 3
     uint64_t *full = reinterpret_cast<uint64_t *>(anew + 3 * NEW);  // [NS]
+    pdl_enter();
     const FusedRep &rp = fa.rep[MR == 1 ? 0 : blockIdx.y];
     const int L = fa.L;
     const int tid = threadIdx.x;
@@ -460,7 +461,18 @@ static cudaError_t fused_rule(const uint32_t *cur, uint32_t *nxt, int L, int R, 
         a.t = t;
         a.err = err;
         a.timeout_ns = timeout_ns;
-        kern<<<dim3((unsigned)(nty * nzb), (unsigned)nr), 256, smem, s>>>(a);
+        // programmatic dependent launch: the next sweep's CTAs are scheduled while this one
+        // drains and wait in pdl_enter for its completion
+        cudaLaunchConfig_t lc = {};
+        lc.gridDim = dim3((unsigned)(nty * nzb), (unsigned)nr);
+        lc.blockDim = dim3(256);
+        lc.dynamicSmemBytes = smem;
+        lc.stream = s;
+        cudaLaunchAttribute attr[1] = {pdl_attribute()};
+        lc.attrs = attr;
+        lc.numAttrs = 1;
+        e = cudaLaunchKernelEx(&lc, kern, a);
+        if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
 }

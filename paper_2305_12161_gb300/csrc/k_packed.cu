@@ -227,6 +227,7 @@ __global__ void __launch_bounds__(256) k_sweep_zfast(uint32_t *lat, Geom g, int 
     constexpr int NS = 5;               // slots: planes z, z+1 being read, z+2, z+3 in flight, 1 spare
     constexpr int RW = 32 / W4;         // rows per warp
     __shared__ uint4 ring[NS * OSZ];
+    pdl_enter();
     const int L = g.L;
     const int tid = threadIdx.x;
     const int nty = L / TY;
@@ -515,13 +516,22 @@ static cudaError_t half_sweep_rule(uint32_t *lat, int L, int R, uint64_t seed, i
     if (cfg.variant == VARIANT_ZFAST) {
         const int W4 = L / 256;
         const dim3 grid((unsigned)((L / (256 / W4)) * (L / cfg.tile_z)), (unsigned)R);
+        // programmatic dependent launch: the next half-sweep's CTAs are scheduled while this
+        // one drains and wait in pdl_enter for its completion
+        cudaLaunchConfig_t lc = {};
+        lc.gridDim = grid;
+        lc.blockDim = dim3(256);
+        lc.stream = s;
+        cudaLaunchAttribute attr[1] = {pdl_attribute()};
+        lc.attrs = attr;
+        lc.numAttrs = 1;
+        const int tz = cfg.tile_z;
         switch (W4) {
-        case 1: k_sweep_zfast<RULE, 1><<<grid, 256, 0, s>>>(lat, g, q, t, seed, cfg.tile_z); break;
-        case 2: k_sweep_zfast<RULE, 2><<<grid, 256, 0, s>>>(lat, g, q, t, seed, cfg.tile_z); break;
-        case 4: k_sweep_zfast<RULE, 4><<<grid, 256, 0, s>>>(lat, g, q, t, seed, cfg.tile_z); break;
-        default: k_sweep_zfast<RULE, 8><<<grid, 256, 0, s>>>(lat, g, q, t, seed, cfg.tile_z); break;
+        case 1: return cudaLaunchKernelEx(&lc, k_sweep_zfast<RULE, 1>, lat, g, q, t, seed, tz);
+        case 2: return cudaLaunchKernelEx(&lc, k_sweep_zfast<RULE, 2>, lat, g, q, t, seed, tz);
+        case 4: return cudaLaunchKernelEx(&lc, k_sweep_zfast<RULE, 4>, lat, g, q, t, seed, tz);
+        default: return cudaLaunchKernelEx(&lc, k_sweep_zfast<RULE, 8>, lat, g, q, t, seed, tz);
         }
-        return cudaGetLastError();
     }
     if (cfg.variant == VARIANT_ZMARCH) {
         const int W4 = L / 256;

@@ -114,6 +114,8 @@ def lib() -> ctypes.CDLL:
                 "ising_batch_set_streamed": (ctypes.c_int, [vp, ctypes.c_int]),
                 "ising_batch_set_class_opts": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ising_opts)]),
                 "ising_batch_get_class_opts": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ising_opts)]),
+                "ising_batch_set_overlap": (ctypes.c_int, [vp, ctypes.c_int]),
+                "ising_batch_overlap": (ctypes.c_int, [vp]),
                 "ising_batch_streamed_classes": (ctypes.c_int, [vp]),
                 "ising_batch_inject_missing_cta": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_double]),
                 "ising_batch_last_error": (ctypes.c_char_p, [vp]),
@@ -482,6 +484,14 @@ class Batch:
         lib().ising_default_opts(ctypes.byref(o))
         o.variant, o.tile_y, o.tile_z, o.depth = variant, tile_y, tile_z, depth
         self._check(lib().ising_batch_set_class_opts(self._h, cls, ctypes.byref(o)), "ising_batch_set_class_opts")
+
+    def set_overlap(self, on: bool) -> None:
+        """Streamed classes beside (True) or after (False) the persistent launch."""
+        self._check(lib().ising_batch_set_overlap(self._h, int(bool(on))), "ising_batch_set_overlap")
+
+    @property
+    def overlap(self) -> bool:
+        return bool(lib().ising_batch_overlap(self._h))
 
     def class_config(self, cls: int) -> dict:
         """Sweep kernel of class ``cls``: variant -1 for the persistent kernel."""

@@ -119,9 +119,10 @@ def test_tuned_plan_changes_speed_not_results(ising):
         b.reinit()
         b.sweep(6)
         got = [b.get_packed(ci, r) for ci, (L, R, s) in enumerate(classes) for r in range(R)]
-        # three work-list rounds of 2 MCS, then for the one streamed class two candidates,
-        # each timed as a warm-up segment of 2 MCS and a timed one of 4
-        assert t_after == 6 + 2 * (2 + 4)
+        # three work-list rounds of 2 MCS, then for the one streamed class two candidates and
+        # the streamed classes after and beside the persistent launch, each timed as a warm-up
+        # segment of 2 MCS and a timed one of 4
+        assert t_after == 6 + 2 * (2 + 4) + 2 * (2 + 4)
         assert kern["variant"] > 0 and b.class_config(0)["variant"] == -1
         for x, y in zip(got, ref):
             assert np.array_equal(x, y)
@@ -132,6 +133,37 @@ def test_tuned_plan_changes_speed_not_results(ising):
             got = [b.get_packed(ci, r) for ci, (L, R, s) in enumerate(classes) for r in range(R)]
             for x, y in zip(got, ref):
                 assert np.array_equal(x, y)
+
+
+def test_streamed_classes_beside_the_persistent_launch(ising):
+    # the same trajectories whether the streamed classes run after the persistent launch or
+    # beside it on their own streams (step by step and as a captured schedule)
+    classes = [(64, 6, 3), (128, 2, 30), (256, 3, 60), (512, 1, 90)]
+    times = [1, 4, 7, 12]
+    out = {}
+    for on in (False, True):
+        with ising.Batch(classes) as b:
+            b.set_overlap(on)
+            assert b.overlap == on
+            b.sweep(5)
+            b.sweep(4)
+            rec, _ = b.measure_ex()
+            packed = [b.get_packed(ci, r) for ci, (L, R, _) in enumerate(classes) for r in range(R)]
+            b.reinit()
+            g, _ = b.run(times)
+            out[on] = (rec, packed, g)
+    assert np.array_equal(out[False][0], out[True][0])
+    for x, y in zip(out[False][1], out[True][1]):
+        assert np.array_equal(x, y)
+    assert np.array_equal(out[False][2], out[True][2])
+    with ising.Batch(classes[2:]) as b:  # streamed classes only: nothing to overlap
+        b.set_overlap(True)
+        b.sweep(3)
+        for ci, (L, R, seed) in enumerate(classes[2:]):
+            with ising.Ising(L, replicas=R, seed=seed) as q:
+                q.sweep(3)
+                for r in range(R):
+                    assert np.array_equal(b.get_packed(ci, r), q.get_packed(r))
 
 
 def test_missing_group_member_times_out_instead_of_hanging(ising):
