@@ -92,6 +92,13 @@ typedef struct {
     int block_x;    /* double checkerboard: block sides in sites (0 = default: block_x = L, */
     int block_y;    /*   block_y = 16, block_z = 8, both L when L <= 16); see ising_scheme */
     int block_z;
+    int pdl;        /* 1 (ising_default_opts): the z-marching (variant 3) and whole-sweep
+                       (variant 5) kernels are launched with programmatic dependent launch:
+                       a sweep's CTAs are scheduled while the previous one drains and wait
+                       for its completion before they touch memory (same results, shorter
+                       gaps between the launches of one stream); 0: plain stream order,
+                       which leaves the SMs of a draining kernel to other streams (many
+                       contexts sharing the GPU); any other value is ISING_EINVAL */
 } ising_opts;
 
 /* Method of the correlation sums (identical results).  POPCOUNT: XOR + bit counts over

@@ -240,7 +240,7 @@ int enqueue_segment(ising_batch *b, int64_t n, unsigned long long *cta_ns)
                 if (even)
                     BCK(b, launch_sweeps_fused(&cur, &nxt, k.L, k.R, k.seed, b->rule, b->t, even, 0, k.cfg.tile_z,
                                                k.cfg.depth, b->d_status, (double)b->timeout_ns * 1e-9, st,
-                                               &b->launches));
+                                               &b->launches, k.cfg.pdl != 0));
                 if (chunk & 1)
                     BCK(b, launch_sweeps_packed(k.lat, k.L, k.R, k.seed, b->rule, b->t + even, 1, 0,
                                                 default_sweep_config(k.L, k.R), st, &b->launches));

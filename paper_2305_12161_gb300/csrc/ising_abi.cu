@@ -149,6 +149,7 @@ void ising_default_opts(ising_opts *o)
     o->block_x = 0;
     o->block_y = 0;
     o->block_z = 0;
+    o->pdl = 1;
 }
 
 int64_t ising_record_len(int L)
@@ -242,6 +243,8 @@ int resolve_opts(int L, int R, const ising_opts &o, SweepConfig *cfg_out, DcbGeo
         return ISING_EINVAL;
     SweepConfig cfg{};
     if (!resolve_sweep_config(L, R, o.variant, o.tile_y, o.tile_z, o.depth, &cfg)) return ISING_EINVAL;
+    if (o.pdl != 0 && o.pdl != 1) return ISING_EINVAL;
+    cfg.pdl = o.pdl;
     if (cfg_out) *cfg_out = cfg;
     if (dcb_out) *dcb_out = dcb;
     return ISING_OK;
@@ -409,7 +412,8 @@ int ising_sweep(ising_ctx *c, int64_t n)
                                 &c->launches);
     else if (c->cfg.variant == VARIANT_ZFUSE)
         e = launch_sweeps_fused(&c->lat, &c->lat_alt, c->L, c->R, c->seed, c->opts.tie, c->t, n, c->opts.cycle,
-                                c->cfg.tile_z, c->cfg.depth, c->dev_err, c->wait_timeout_s, c->stream, &c->launches);
+                                c->cfg.tile_z, c->cfg.depth, c->dev_err, c->wait_timeout_s, c->stream, &c->launches,
+                                c->cfg.pdl != 0);
     else
         e = launch_sweeps_packed(c->lat, c->L, c->R, c->seed, c->opts.tie, c->t, n, c->opts.cycle, c->cfg, c->stream,
                                  &c->launches);

@@ -431,7 +431,7 @@ static FusedRep fused_rep(const uint32_t *cur, uint32_t *nxt, int64_t nw, int r,
 // per replica with its arguments as the kernel's only parameters.
 template <int RULE, int W4, int NS, bool BAL, bool MULTI>
 static cudaError_t fused_rule(const uint32_t *cur, uint32_t *nxt, int L, int R, uint64_t seed, int mixed, uint32_t t,
-                              int TZ, bool fit, int *err, uint64_t timeout_ns, cudaStream_t s)
+                              int TZ, bool fit, int *err, uint64_t timeout_ns, cudaStream_t s, bool pdl)
 {
     constexpr int MR = MULTI ? FUSED_MAXR : 1;
     constexpr size_t smem = fused_smem_bytes<W4, NS, BAL>();
@@ -470,7 +470,7 @@ static cudaError_t fused_rule(const uint32_t *cur, uint32_t *nxt, int L, int R, 
         lc.stream = s;
         cudaLaunchAttribute attr[1] = {pdl_attribute()};
         lc.attrs = attr;
-        lc.numAttrs = 1;
+        lc.numAttrs = pdl ? 1 : 0;
         e = cudaLaunchKernelEx(&lc, kern, a);
         if (e != cudaSuccess) return e;
     }
@@ -479,13 +479,13 @@ static cudaError_t fused_rule(const uint32_t *cur, uint32_t *nxt, int L, int R, 
 
 template <int RULE, int NS, bool BAL, bool MULTI>
 static cudaError_t fused_one(const uint32_t *cur, uint32_t *nxt, int L, int R, uint64_t seed, int mixed, uint32_t t,
-                             int TZ, bool fit, int *err, uint64_t timeout_ns, cudaStream_t s)
+                             int TZ, bool fit, int *err, uint64_t timeout_ns, cudaStream_t s, bool pdl)
 {
     switch (L / 256) {
-    case 1: return fused_rule<RULE, 1, NS, BAL, MULTI>(cur, nxt, L, R, seed, mixed, t, TZ, fit, err, timeout_ns, s);
-    case 2: return fused_rule<RULE, 2, NS, BAL, MULTI>(cur, nxt, L, R, seed, mixed, t, TZ, fit, err, timeout_ns, s);
-    case 4: return fused_rule<RULE, 4, NS, BAL, MULTI>(cur, nxt, L, R, seed, mixed, t, TZ, fit, err, timeout_ns, s);
-    case 8: return fused_rule<RULE, 8, NS, BAL, MULTI>(cur, nxt, L, R, seed, mixed, t, TZ, fit, err, timeout_ns, s);
+    case 1: return fused_rule<RULE, 1, NS, BAL, MULTI>(cur, nxt, L, R, seed, mixed, t, TZ, fit, err, timeout_ns, s, pdl);
+    case 2: return fused_rule<RULE, 2, NS, BAL, MULTI>(cur, nxt, L, R, seed, mixed, t, TZ, fit, err, timeout_ns, s, pdl);
+    case 4: return fused_rule<RULE, 4, NS, BAL, MULTI>(cur, nxt, L, R, seed, mixed, t, TZ, fit, err, timeout_ns, s, pdl);
+    case 8: return fused_rule<RULE, 8, NS, BAL, MULTI>(cur, nxt, L, R, seed, mixed, t, TZ, fit, err, timeout_ns, s, pdl);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -494,27 +494,27 @@ static cudaError_t fused_one(const uint32_t *cur, uint32_t *nxt, int L, int R, u
 // kernel is built for these forms only).
 template <int RULE, bool BAL>
 static cudaError_t fused_five(const uint32_t *cur, uint32_t *nxt, int L, int R, uint64_t seed, int mixed, uint32_t t,
-                              int TZ, bool fit, int *err, uint64_t timeout_ns, cudaStream_t s)
+                              int TZ, bool fit, int *err, uint64_t timeout_ns, cudaStream_t s, bool pdl)
 {
-    if (R > 1) return fused_one<RULE, 5, BAL, true>(cur, nxt, L, R, seed, mixed, t, TZ, fit, err, timeout_ns, s);
-    return fused_one<RULE, 5, BAL, false>(cur, nxt, L, R, seed, mixed, t, TZ, fit, err, timeout_ns, s);
+    if (R > 1) return fused_one<RULE, 5, BAL, true>(cur, nxt, L, R, seed, mixed, t, TZ, fit, err, timeout_ns, s, pdl);
+    return fused_one<RULE, 5, BAL, false>(cur, nxt, L, R, seed, mixed, t, TZ, fit, err, timeout_ns, s, pdl);
 }
 
 // depth = copy groups in flight while a step computes: 1..3 (four to six slots; 0 = 2); +8:
 // the balanced tiling; +16: z-blocks fitted to the resident CTAs
 template <int RULE>
 static cudaError_t fused_depth(const uint32_t *cur, uint32_t *nxt, int L, int R, uint64_t seed, int mixed,
-                               uint32_t t, int TZ, int depth, int *err, uint64_t timeout_ns, cudaStream_t s)
+                               uint32_t t, int TZ, int depth, int *err, uint64_t timeout_ns, cudaStream_t s, bool pdl)
 {
     const bool fit = depth & 16;
     switch (depth & ~16) {
-    case 1: return fused_one<RULE, 4, false, false>(cur, nxt, L, R, seed, mixed, t, TZ, fit, err, timeout_ns, s);
-    case 3: return fused_one<RULE, 6, false, false>(cur, nxt, L, R, seed, mixed, t, TZ, fit, err, timeout_ns, s);
-    case 9: return fused_one<RULE, 4, true, false>(cur, nxt, L, R, seed, mixed, t, TZ, fit, err, timeout_ns, s);
+    case 1: return fused_one<RULE, 4, false, false>(cur, nxt, L, R, seed, mixed, t, TZ, fit, err, timeout_ns, s, pdl);
+    case 3: return fused_one<RULE, 6, false, false>(cur, nxt, L, R, seed, mixed, t, TZ, fit, err, timeout_ns, s, pdl);
+    case 9: return fused_one<RULE, 4, true, false>(cur, nxt, L, R, seed, mixed, t, TZ, fit, err, timeout_ns, s, pdl);
     case 8:
-    case 10: return fused_five<RULE, true>(cur, nxt, L, R, seed, mixed, t, TZ, fit, err, timeout_ns, s);
-    case 11: return fused_one<RULE, 6, true, false>(cur, nxt, L, R, seed, mixed, t, TZ, fit, err, timeout_ns, s);
-    default: return fused_five<RULE, false>(cur, nxt, L, R, seed, mixed, t, TZ, fit, err, timeout_ns, s);
+    case 10: return fused_five<RULE, true>(cur, nxt, L, R, seed, mixed, t, TZ, fit, err, timeout_ns, s, pdl);
+    case 11: return fused_one<RULE, 6, true, false>(cur, nxt, L, R, seed, mixed, t, TZ, fit, err, timeout_ns, s, pdl);
+    default: return fused_five<RULE, false>(cur, nxt, L, R, seed, mixed, t, TZ, fit, err, timeout_ns, s, pdl);
     }
 }
 
@@ -529,7 +529,7 @@ static int64_t fused_launches_per_sweep(int R, int depth)
 
 cudaError_t launch_sweeps_fused(uint32_t **cur, uint32_t **nxt, int L, int R, uint64_t seed, int rule, int64_t t0,
                                 int64_t n_mcs, int cycle, int TZ, int depth, int *err, double timeout_s,
-                                cudaStream_t s, int64_t *launches)
+                                cudaStream_t s, int64_t *launches, bool pdl)
 {
     const uint64_t timeout_ns = (uint64_t)(timeout_s * 1e9);
     for (int64_t k = 0; k < n_mcs; ++k) {
@@ -537,12 +537,12 @@ cudaError_t launch_sweeps_fused(uint32_t **cur, uint32_t **nxt, int L, int R, ui
         cudaError_t e;
         switch (rule) {
         case TIE_GLAUBER:
-            e = fused_depth<TIE_GLAUBER>(*cur, *nxt, L, R, seed, cycle, t, TZ, depth, err, timeout_ns, s);
+            e = fused_depth<TIE_GLAUBER>(*cur, *nxt, L, R, seed, cycle, t, TZ, depth, err, timeout_ns, s, pdl);
             break;
         case TIE_ALWAYS:
-            e = fused_depth<TIE_ALWAYS>(*cur, *nxt, L, R, seed, cycle, t, TZ, depth, err, timeout_ns, s);
+            e = fused_depth<TIE_ALWAYS>(*cur, *nxt, L, R, seed, cycle, t, TZ, depth, err, timeout_ns, s, pdl);
             break;
-        default: e = fused_depth<TIE_NEVER>(*cur, *nxt, L, R, seed, cycle, t, TZ, depth, err, timeout_ns, s); break;
+        default: e = fused_depth<TIE_NEVER>(*cur, *nxt, L, R, seed, cycle, t, TZ, depth, err, timeout_ns, s, pdl); break;
         }
         if (e != cudaSuccess) return e;
         uint32_t *tmp = *cur;  // the new sweep becomes the current store

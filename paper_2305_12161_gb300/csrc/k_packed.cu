@@ -516,15 +516,15 @@ static cudaError_t half_sweep_rule(uint32_t *lat, int L, int R, uint64_t seed, i
     if (cfg.variant == VARIANT_ZFAST) {
         const int W4 = L / 256;
         const dim3 grid((unsigned)((L / (256 / W4)) * (L / cfg.tile_z)), (unsigned)R);
-        // programmatic dependent launch: the next half-sweep's CTAs are scheduled while this
-        // one drains and wait in pdl_enter for its completion
+        // programmatic dependent launch (cfg.pdl): the next half-sweep's CTAs are scheduled
+        // while this one drains and wait in pdl_enter for its completion
         cudaLaunchConfig_t lc = {};
         lc.gridDim = grid;
         lc.blockDim = dim3(256);
         lc.stream = s;
         cudaLaunchAttribute attr[1] = {pdl_attribute()};
         lc.attrs = attr;
-        lc.numAttrs = 1;
+        lc.numAttrs = cfg.pdl ? 1 : 0;
         const int tz = cfg.tile_z;
         switch (W4) {
         case 1: return cudaLaunchKernelEx(&lc, k_sweep_zfast<RULE, 1>, lat, g, q, t, seed, tz);

@@ -26,6 +26,7 @@ struct SweepConfig {
     int tile_y;  // rows per tile (z-march; ZFAST: fixed to 256 / (L/256))
     int tile_z;  // planes per tile (z-march)
     int depth;   // ZDEEP: planes in flight beyond the one consumed (2..4)
+    int pdl = 1; // ZFAST, ZFUSE: programmatic dependent launch (0: plain stream order)
 };
 
 bool sweep_config_valid(int L, const SweepConfig &c);
@@ -43,7 +44,7 @@ bool resolve_sweep_config(int L, int R, int variant, int tile_y, int tile_z, int
 bool fused_config_valid(int L, int tile_z, int depth);
 cudaError_t launch_sweeps_fused(uint32_t **cur, uint32_t **nxt, int L, int R, uint64_t seed, int rule, int64_t t0,
                                 int64_t n_mcs, int cycle, int tile_z, int depth, int *err, double timeout_s,
-                                cudaStream_t s, int64_t *launches);
+                                cudaStream_t s, int64_t *launches, bool pdl = true);
 
 // n_mcs sweeps from completed-sweep count t0; returns the number of launches through
 // *launches.

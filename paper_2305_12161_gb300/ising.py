@@ -48,7 +48,7 @@ class ising_opts(ctypes.Structure):
                 ("device", ctypes.c_int), ("variant", ctypes.c_int), ("tile_y", ctypes.c_int),
                 ("tile_z", ctypes.c_int), ("depth", ctypes.c_int), ("cycle", ctypes.c_int), ("corr", ctypes.c_int),
                 ("scheme", ctypes.c_int), ("block_x", ctypes.c_int), ("block_y", ctypes.c_int),
-                ("block_z", ctypes.c_int)]
+                ("block_z", ctypes.c_int), ("pdl", ctypes.c_int)]
 
 
 def lib_path() -> str:
@@ -199,11 +199,12 @@ class Ising:
     def __init__(self, L: int, replicas: int = 1, seed: int = 1, tie: int = TIE_GLAUBER, form: int = FORM_PACKED,
                  stream=None, device: int = -1, variant: int = 0, tile_y: int = 0, tile_z: int = 0, depth: int = 0,
                  cycle: int = CYCLE_01, corr: int = CORR_AUTO, scheme: int = SCHEME_CHECKERBOARD,
-                 block=(0, 0, 0)):
+                 block=(0, 0, 0), pdl: int = 1):
         self._h = ctypes.c_void_p()
         o = ising_opts()
         lib().ising_default_opts(ctypes.byref(o))
         o.tie, o.form, o.device, o.variant, o.tile_y, o.tile_z, o.depth = tie, form, device, variant, tile_y, tile_z, depth
+        o.pdl = pdl
         o.cycle = cycle
         o.corr = corr
         o.scheme = scheme

@@ -100,17 +100,20 @@ class _Active:
 
 
 class QuenchServer:
-    """`tune`: pick each lattice size's sweep kernel and tiling with the library's autotuner
-    the first time a request of that size is submitted (every choice gives the same results;
-    the fused whole-sweep kernel, which the tuner picks for the larger sizes, holds a second
-    packed store, which the admission footprint counts)."""
+    """`tune`: pick the sweep kernel and tiling of each request shape (lattice size and
+    replica count) with the library's autotuner the first time a request of that shape is
+    submitted (every choice gives the same results; the best kernel depends on the replica
+    count as well as the size, since replicas share a launch; the fused whole-sweep kernel,
+    which the tuner picks for the larger sizes, holds a second packed store, which the
+    admission footprint counts)."""
 
     def __init__(self, budget_bytes: float = 150e9, max_slots: int = 16, quantum_mcs: int = 64,
-                 max_inflight: int = 2, c: float = 0.5, tune: bool = True):
+                 max_inflight: int = 2, c: float = 0.5, tune: bool = True, pdl: int = 1):
         import torch
         self.torch = torch
         self.tune = tune
-        self.opts: dict[int, dict] = {}  # L -> context options
+        self.pdl = pdl  # programmatic dependent launch of the sweep kernels (ising_opts.pdl)
+        self.opts: dict[tuple, dict] = {}  # (L, replicas) -> context options
         self.budget = float(budget_bytes)
         self.max_slots = max_slots
         self.quantum = quantum_mcs
@@ -126,18 +129,21 @@ class QuenchServer:
     def now(self) -> float:
         return time.perf_counter() - self.t0
 
-    def options_for(self, L: int) -> dict:
-        """Context options of requests of size L (autotuned once per size when `tune`)."""
-        if L not in self.opts:
+    def options_for(self, L: int, replicas: int = 1) -> dict:
+        """Context options of requests of size L with `replicas` lattices (autotuned once per
+        shape when `tune`)."""
+        key = (L, replicas)
+        if key not in self.opts:
             o = {}
             if self.tune:
-                t = ising.ising_tune_sweep(L, 1, probe_mcs=4)
+                t = ising.ising_tune_sweep(L, replicas, probe_mcs=4)
                 o = {k: t[k] for k in ("variant", "tile_y", "tile_z", "depth")}
-            self.opts[L] = o
-        return self.opts[L]
+            o["pdl"] = self.pdl
+            self.opts[key] = o
+        return self.opts[key]
 
     def footprint(self, req: Request) -> int:
-        return footprint_bytes(req.L, req.replicas, req.K, **self.options_for(req.L))
+        return footprint_bytes(req.L, req.replicas, req.K, **self.options_for(req.L, req.replicas))
 
     def submit(self, req: Request) -> None:
         if self.footprint(req) > self.budget:
@@ -148,7 +154,7 @@ class QuenchServer:
         admitted, self.pending, self.used = admit(self.pending, len(self.active), self.used, self.budget,
                                                   self.max_slots, self.footprint)
         for req in admitted:
-            self.active.append(_Active(req, self.now(), self.torch, self.options_for(req.L)))
+            self.active.append(_Active(req, self.now(), self.torch, self.options_for(req.L, req.replicas)))
 
     def _issue(self, a: _Active) -> None:
         # one quantum: sweep towards the next measured time, measure when it is reached
@@ -182,9 +188,9 @@ class QuenchServer:
 
     def run(self, trace: list[Request], idle_sleep_s: float = 0.0005) -> list[Result]:
         """Serve `trace` (arrival_s relative to the start) until every request is done.  The
-        sizes in the trace are tuned before the clock starts."""
+        request shapes in the trace are tuned before the clock starts."""
         for r in trace:
-            self.options_for(r.L)
+            self.options_for(r.L, r.replicas)
         self.t0 = time.perf_counter()
         queue = sorted(trace, key=lambda r: r.arrival_s)
         i = 0

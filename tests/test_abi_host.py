@@ -68,7 +68,8 @@ def test_create_rejects_bad_arguments_before_touching_a_device(lib):
     bad = (dict(L=64, variant=9), dict(L=128, variant=ising.VARIANT_ZFUSE), dict(L=2048, variant=ising.VARIANT_ZFUSE,
            depth=7), dict(L=2048, variant=ising.VARIANT_ZFUSE, tile_z=3), dict(L=2048, variant=ising.VARIANT_ZFAST,
            tile_z=48), dict(L=1024, variant=ising.VARIANT_ZDEEP, depth=5), dict(L=96 * 4, variant=ising.VARIANT_ZFAST),
-           dict(L=2048, variant=ising.VARIANT_ZFUSE, depth=33), dict(L=2048, variant=ising.VARIANT_ZFUSE, depth=64))
+           dict(L=2048, variant=ising.VARIANT_ZFUSE, depth=33), dict(L=2048, variant=ising.VARIANT_ZFUSE, depth=64),
+           dict(L=256, pdl=2), dict(L=256, variant=ising.VARIANT_ZFAST, pdl=-1))
     for kw in bad:
         o = ising.ising_opts()
         lib.ising_default_opts(ctypes.byref(o))
@@ -82,7 +83,8 @@ def test_create_rejects_bad_arguments_before_touching_a_device(lib):
     good = (dict(L=64), dict(L=256, variant=ising.VARIANT_ZFAST, tile_z=8), dict(L=2048, variant=ising.VARIANT_ZFUSE,
             tile_z=32, depth=3), dict(L=1024, variant=ising.VARIANT_ZFUSE, tile_z=32, depth=10),
             dict(L=512, variant=ising.VARIANT_ZDEEP, tile_z=16, depth=4), dict(L=2048, variant=ising.VARIANT_ZFUSE,
-            tile_z=64, depth=27))
+            tile_z=64, depth=27), dict(L=256, variant=ising.VARIANT_ZFAST, pdl=0),
+            dict(L=256, variant=ising.VARIANT_ZFUSE, tile_z=8, depth=18, pdl=0))
     for kw in good:
         o = ising.ising_opts()
         lib.ising_default_opts(ctypes.byref(o))

@@ -125,3 +125,22 @@ def test_batch_streamed_classes_on_the_fused_kernel(ising):
                     qrec = q.measure()
                     for r in range(R):
                         assert np.array_equal(b.record_of(g1[k], ci, r), qrec[r]), (L, r, tk)
+
+
+@pytest.mark.parametrize("kw", [dict(variant=3, tile_z=8), dict(variant=5, tile_z=8, depth=18),
+                                dict(variant=5, tile_z=32, depth=10)])
+def test_plain_stream_order_gives_the_same_trajectory(ising, kw):
+    # programmatic dependent launch (the default) and plain stream order: same spins
+    L, R, seed, n = 256, 3, 55, 7
+    got = {}
+    for pdl in (0, 1):
+        with ising.Ising(L, replicas=R, seed=seed, pdl=pdl, **kw) as q:
+            q.sweep(n)
+            got[pdl] = [q.get_packed(r) for r in range(R)]
+    for a, b in zip(got[0], got[1]):
+        assert np.array_equal(a, b)
+    want = oracle.init(L, seed, 2)
+    oracle.sweeps(want, 0, n, seed + 2)
+    with ising.Ising(L, replicas=1, seed=seed + 2) as q:
+        q.set_spins(want, 0)
+        assert np.array_equal(got[0][2], q.get_packed(0))
