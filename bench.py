@@ -162,7 +162,7 @@ BATCH_CLASSES = [(64, 512, 1), (128, 64, 513), (256, 16, 577), (512, 4, 593)]  #
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch from one ncu capture of
 # the kernel as built (the file under profiles/ gives the command), by (kernel, L, tile_z,
 # depth); kernels changed since their capture and configurations never captured report null
-TRAFFIC_NCU = {("k_mcs_fused", 2048, 64, 26): (2.163e9, "ncu, profiles/k_mcs_fused_L2048.md (balanced tiling, "
+TRAFFIC_NCU = {("k_mcs_fused", 2048, 64, 26): (2.162e9, "ncu, profiles/k_mcs_fused_L2048.md (balanced tiling, "
                                                         "z-blocks fitted near 64 planes, five slots)")}
 
 
