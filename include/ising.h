@@ -116,8 +116,9 @@ typedef enum { ISING_CORR_AUTO = 0, ISING_CORR_POPCOUNT = 1, ISING_CORR_TENSOR =
  * runs, Methods).  MIXED: the first sublattice of each sweep is random (Supp. Methods I B,
  * the "mixed cycle" that restores detailed balance): sweep t of the lattice keyed S goes
  * blue first when bit 0 of word 0 of Philox(counter (0, t, 5, 0), key S) is 1.  With
- * replicas > 1 each replica draws its own order (one launch per replica and half-sweep).
- * The batched form supports the 01 cycle only. */
+ * replicas > 1 each replica draws its own order (the half-sweep kernels launch once per
+ * replica and half-sweep; the whole-sweep kernel carries each replica's order in its
+ * parameters).  The batched form supports the 01 cycle only. */
 typedef enum { ISING_CYCLE_01 = 0, ISING_CYCLE_MIXED = 1 } ising_cycle;
 
 /* Update scheme of a sweep.  CHECKERBOARD: the two half-sweeps of the main text (Methods).

@@ -1,7 +1,9 @@
 // C ABI of the batched form (declared in include/ising.h): a batch of lattice classes
 // (L, replicas, seed) advanced together by one persistent cooperative launch per run
-// segment, measured per class with the single-lattice measurement kernels, and a whole
-// log-spaced schedule (segments + measurements) captured into one CUDA graph.
+// segment, with the larger classes streamed beside it by single-lattice sweep kernels on
+// side streams, measured per class (one class per stream) with the single-lattice
+// measurement kernels, and a whole log-spaced schedule (segments + measurements) captured
+// into one CUDA graph.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -296,7 +298,7 @@ int read_status(ising_batch *b)
     return ISING_OK;
 }
 
-// Split the classes between the persistent kernel and the z-marching kernel, rebuild the
+// Split the classes between the persistent kernel and the single-lattice kernels, rebuild the
 // persistent kernel's lattice list, shared-memory size, occupancy and work list.
 int assign_modes(ising_batch *b)
 {

@@ -38,9 +38,11 @@ bool resolve_sweep_config(int L, int R, int variant, int tile_y, int tile_z, int
 // depth: copy groups in flight while a step computes, 1..3 (0 = 2; SweepConfig.depth); +8 selects
 // the balanced tiling (tiles of 256/(L/256) - 2 rows, the halo rows computed by ordinary threads;
 // 2 or 3 groups); +16 fits the number of z-blocks (tiles of nearly equal depth, within 25% of
-// tile_z) to the resident CTAs so that the launch's last wave is nearly full.  The kernel
-// launches once per replica and bounds its waits for copies by
-// timeout_s of wall time; one that gives up sets *err = 4 (the sweep's results are then invalid).
+// tile_z) to the resident CTAs so that the launch's last wave is nearly full.  The five-slot
+// forms (depth 0, 2, 8, 10 with or without +16) take up to 16 replicas per launch, the others
+// one; every replica has its own first sublattice under the mixed cycle.  The kernel bounds
+// its waits for copies by timeout_s of wall time; one that gives up sets *err = 4 (the
+// sweep's results are then invalid).  pdl: programmatic dependent launch.
 bool fused_config_valid(int L, int tile_z, int depth);
 cudaError_t launch_sweeps_fused(uint32_t **cur, uint32_t **nxt, int L, int R, uint64_t seed, int rule, int64_t t0,
                                 int64_t n_mcs, int cycle, int tile_z, int depth, int *err, double timeout_s,
