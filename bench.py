@@ -100,17 +100,28 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(sample_L: int = 1024, mcs: int = 2) -> dict:
-    """The oracle as it stands, on this host's cores, on a bounded sample."""
+def cpu_baseline(sample_L: int = 1024, mcs: int = 2, single_L: int = 256, single_mcs: int = 2) -> dict:
+    """The oracle as it stands, on this host's cores, on a bounded sample; and on one core,
+    on a smaller sample."""
     import oracle
     cores = oracle.set_threads(os.cpu_count() or 1)
     s = oracle.init(sample_L, 1)
     t0 = time.perf_counter()
     oracle.sweeps(s, 0, mcs, 1, oracle.TIE_GLAUBER)
     dt = time.perf_counter() - t0
+    del s
+    oracle.set_threads(1)
+    s1 = oracle.init(single_L, 1)
+    t1 = time.perf_counter()
+    oracle.sweeps(s1, 0, single_mcs, 1, oracle.TIE_GLAUBER)
+    dt1 = time.perf_counter() - t1
+    oracle.set_threads(cores)
     return {"value": mcs * sample_L**3 / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{mcs} MCS of one {sample_L}^3 lattice from the T=inf start (sweeps only, "
-                      f"no correlation pass), {dt:.1f} s"}
+                      f"no correlation pass), {dt:.1f} s",
+            "single_thread": {"value": single_mcs * single_L**3 / dt1 / 1e9, "unit": UNIT, "cores": 1,
+                              "sample": f"{single_mcs} MCS of one {single_L}^3 lattice from the T=inf start, "
+                                        f"{dt1:.1f} s"}}
 
 
 def run_reference(args):

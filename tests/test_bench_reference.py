@@ -25,3 +25,14 @@ def test_reference_arm_prints_the_contract_line():
     assert d["cpu_baseline"]["value"] == d["value"] == d["e2e"]["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert "workload" in d["config"]
+
+
+def test_cpu_baseline_reports_all_cores_and_one_core():
+    sys.path.insert(0, ROOT)
+    import bench
+    cb = bench.cpu_baseline(sample_L=32, mcs=1, single_L=16, single_mcs=1)
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] > 0
+    one = cb["single_thread"]
+    assert one["cores"] == 1 and one["value"] > 0 and one["unit"] == cb["unit"]
+    import oracle
+    assert oracle.set_threads(cb["cores"]) == cb["cores"]  # the thread count is put back
