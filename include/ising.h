@@ -314,7 +314,10 @@ int64_t ising_launch_count(const ising_ctx *ctx);
  * random bits), so batching changes speed, not results.
  * Records and derived values are concatenated in class order, replica-major within a
  * class: ising_batch_record_words() int64 and 4 * ising_batch_lattices() doubles per
- * measured time.  Only the PACKED form is batched (opts->form must be PACKED). */
+ * measured time; a measurement runs one class per stream, and classes with L >= 512 take
+ * their correlation sums on the tensor cores (identical results), for which
+ * ising_batch_create allocates 2 L^3 bytes of scratch per such class.  Only the PACKED
+ * form is batched (opts->form must be PACKED). */
 typedef struct ising_batch ising_batch;
 int ising_batch_create(ising_batch **out, int nclass, const int *L, const int *replicas, const uint64_t *seeds,
                        const ising_opts *opts);
