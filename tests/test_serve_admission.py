@@ -60,3 +60,15 @@ def test_admitted_sum_stays_within_budget_and_slots():
         # nothing kept could have been admitted at the end (greedy in arrival order)
         if n_active + len(adm) < slots:
             assert all(used + fps[r.id] > budget for r in keep)
+
+
+def test_options_are_kept_per_request_shape():
+    srv = serve.QuenchServer(tune=False, pdl=0)
+    a = srv.options_for(256, 3)
+    assert a == {"pdl": 0}
+    assert srv.options_for(256, 3) is a  # computed once per shape
+    assert srv.options_for(256, 4) is not a
+    assert set(srv.opts) == {(256, 3), (256, 4)}
+    req = serve.Request(id=0, L=256, t_max=10, replicas=3, seed=1, K=4)
+    # the launch order of the sweep kernels does not change the device footprint
+    assert srv.footprint(req) == serve.footprint_bytes(256, 3, 4) == serve.footprint_bytes(256, 3, 4, pdl=1)
