@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(256, MINB) k_mcs_fused(const __grid_constant__
     const int hB = (hr ? NR + 2 : 1) * W4 + cx;  // halo row in a B slot
     const int hN = (hr ? NR + 1 : 0) * W4 + cx;  // halo row in an A slot
     const int32_t dh = wrapL(hr ? y0 + NR : y0 - 1) * W4 + cx - own;
-    const uint32_t A = rp.A, B = 1u - rp.A;
+    const uint32_t A = rp.A;
 
     // groups 0 and 1 before the first step (step k waits for group k + 2); thread 0 tracks
     // the last group it saw land and the last it issued, for the drain after a failed wait
