@@ -125,6 +125,13 @@ def test_batch_create_rejects_bad_arguments(lib):
     assert lib.ising_batch_create(ctypes.byref(h), 0, None, None, None, None) == ising.ISING_EINVAL
     assert lib.ising_batch_destroy(None) == ising.ISING_OK
     assert lib.ising_batch_sweep(None, 1) == ising.ISING_EINVAL
+    o = ising.ising_opts()
+    lib.ising_default_opts(ctypes.byref(o))
+    assert o.pdl == 1  # programmatic dependent launch is the default
+    assert lib.ising_batch_set_class_opts(None, 0, ctypes.byref(o)) == ising.ISING_EINVAL
+    assert lib.ising_batch_get_class_opts(None, 0, ctypes.byref(o)) == ising.ISING_EINVAL
+    assert lib.ising_batch_set_overlap(None, 1) == ising.ISING_EINVAL
+    assert lib.ising_batch_overlap(None) == -1
 
 
 def test_footprint_bytes_counts_every_buffer(lib):
