@@ -180,9 +180,11 @@ TRAFFIC_NCU = {("k_mcs_fused", 2048, 64, 26): (2.162e9, "ncu, profiles/k_mcs_fus
 def run_batched(torch, ising, inputs, K: int = 20, window: int = 20) -> dict:
     """Mixed batch 512x64^3 + 64x128^3 + 16x256^3 + 4x512^3 (each lattice its own seed):
     the batched form runs 10^4 MCS with K log-spaced measurements as one CUDA graph
-    (persistent launch per segment, work list tuned by the autotuner); the plain form
-    (one byte per spin, one launch per lattice) and the packed form launched per class
-    are compared with it on the same window of `window` MCS from the T = inf start."""
+    (per segment a persistent launch for the 64^3 and 128^3 classes and the 256^3 and 512^3
+    classes streamed beside it on side streams; work list, streamed kernels and stream order
+    tuned by the autotuner); the plain form (one byte per spin, one launch per lattice) and
+    the packed form launched per class (on the kernels the batch chose) are compared with it
+    on the same window of `window` MCS from the T = inf start."""
     stream = torch.cuda.Stream()
     times = inputs.log_schedule(10_000, K)
     spins = sum(R * L**3 for L, R, _ in BATCH_CLASSES)
@@ -313,8 +315,9 @@ def aggregate_ranks(ms: float, updates: float, dist=None, device=None) -> tuple[
 
 
 def run_batch_case(args):
-    """A short plain run of the batched form for ncu: the mixed batch, --mcs sweeps in one
-    persistent launch, then one measurement of every lattice."""
+    """A short plain run of the batched form for ncu: the mixed batch, --mcs sweeps as one
+    segment (the persistent launch and the streamed classes' launches beside it), then one
+    measurement of every lattice."""
     import __graft_entry__
     from paper_2305_12161_gb300 import ising
     __graft_entry__.build()
